@@ -1,0 +1,217 @@
+"""FP64 CPU oracle (test infrastructure only).
+
+Plain, slow, obviously-correct double-precision implementation of the
+line-list -> intensity -> cross-section path of PyExoCross 2.0 (Secs. 2.4.2,
+2.4.3, 3.1, 3.2) and of its adjoint.  Only the tests, the smoke check and the
+benchmark's CPU-baseline leg use it; the product path never imports it.  It
+shares no code with the CUDA library (see oracle.c for the equations and the
+readings taken where the text is silent).
+
+Every function is pinned in tests/test_oracle.py against closed forms,
+invariants, SciPy's independent Faddeeva implementation and brute force.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "_oracle.so")
+_lib = None
+
+KIND = {"gauss_doppler": 0, "gauss_hwhm": 1, "lorentz": 2, "voigt": 3}
+STATUS = {0: "ok", 1: "bad argument", 2: "state id out of range", 3: "non-finite input",
+          4: "Boltzmann exponent overflow"}
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c (gcc -O2, OpenMP, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=gnu11",
+                               "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        P, i64, dbl, cint = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+        L.orc_c2.restype = dbl
+        L.orc_faddeeva.argtypes = [i64, P, P, P, P]
+        L.orc_profile.argtypes = [cint, i64, P, dbl, dbl, P, P, P]
+        L.orc_partition.argtypes = [P, P, P, i64, dbl, dbl, P]
+        L.orc_line_intensities.argtypes = [P, P, P, i64, P, P, P, cint, i64, dbl, dbl, dbl,
+                                           dbl, dbl, i64, dbl, dbl, P, P, P, P, P]
+        L.orc_list_exponent.argtypes = [P, P, i64]
+        L.orc_list_exponent.restype = ctypes.c_int32
+        L.orc_scale_intensities.argtypes = [P, P, i64, ctypes.c_int32, P]
+        L.orc_sorted_order.argtypes = [P, P, i64, P]
+        L.orc_sorted_order.restype = i64
+        L.orc_segment_ranges.argtypes = [P, P, i64, i64, i64, P, P]
+        L.orc_widths.argtypes = [cint, P, P, P, i64, dbl, dbl, dbl, dbl, dbl, P, P]
+        L.orc_cross_section.argtypes = [cint, P, P, P, P, P, P, P, i64, dbl, dbl, i64, P]
+        L.orc_cross_section_grad.argtypes = [cint, P, P, P, P, P, cint, P, P, P, P, P, P, P, P, i64,
+                                             dbl, dbl, dbl, dbl, P, dbl, dbl, P, P, P, P, P, P]
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dt):
+    return None if a is None else np.ascontiguousarray(a, dtype=dt)
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code):
+        super().__init__(f"oracle status {code}: {STATUS.get(code, '?')}")
+        self.code = code
+
+
+def _chk(code):
+    if code != 0:
+        raise OracleError(code)
+
+
+def c2() -> float:
+    """Second radiation constant hc/k_B in cm K (CODATA 2018 exact values)."""
+    return _load().orc_c2()
+
+
+def faddeeva(x, y):
+    """w(x + iy) for y >= 0, as complex128."""
+    x = _c(np.atleast_1d(x), np.float64); y = _c(np.broadcast_to(y, x.shape), np.float64)
+    re = np.empty_like(x); im = np.empty_like(x)
+    _load().orc_faddeeva(x.size, _p(x), _p(y), _p(re), _p(im))
+    return re + 1j * im
+
+
+def profile(kind: str, x, alpha: float, gamma: float = 0.0, derivs: bool = False):
+    """f(x) (and df/dalpha, df/dgamma) for one line with HWHMs alpha, gamma."""
+    x = _c(np.atleast_1d(x), np.float64)
+    f = np.empty_like(x); fa = np.empty_like(x); fg = np.empty_like(x)
+    _load().orc_profile(KIND[kind], x.size, _p(x), alpha, gamma, _p(f), _p(fa), _p(fg))
+    return (f, fa, fg) if derivs else f
+
+
+def partition(E, g, E_vib=None, T=296.0, T_vib=0.0):
+    """(Q, dQ/dT or dQ/dT_rot, dQ/dT_vib): Eq. (pf) or Eq. (Q nlte 2T)."""
+    E = _c(E, np.float64); g = _c(g, np.int32); Ev = _c(E_vib, np.float64)
+    out = np.zeros(3)
+    _chk(_load().orc_partition(_p(E), _p(g), _p(Ev), E.size, T, T_vib, _p(out)))
+    return out
+
+
+def line_intensities(E, g, E_vib, upper, lower, A, T, T_vib, Q, nu_min, dnu, n_grid, cut, threshold=0.0):
+    """Per-transition nu, I (cm/molecule, 0 where dropped), keep, ilo, ihi."""
+    E = _c(E, np.float64); g = _c(g, np.int32); Ev = _c(E_vib, np.float64)
+    up = _c(upper, np.int32); lo = _c(lower, np.int32)
+    A_f32 = A.dtype == np.float32
+    A = _c(A, np.float32 if A_f32 else np.float64)
+    n = up.size
+    nu = np.empty(n); I = np.empty(n); keep = np.empty(n, np.uint8)
+    ilo = np.empty(n, np.int64); ihi = np.empty(n, np.int64)
+    _chk(_load().orc_line_intensities(_p(E), _p(g), _p(Ev), E.size, _p(up), _p(lo), _p(A), int(A_f32), n,
+                                      T, T_vib, Q, nu_min, dnu, n_grid, cut, threshold,
+                                      _p(nu), _p(I), _p(keep), _p(ilo), _p(ihi)))
+    return nu, I, keep, ilo, ihi
+
+
+def list_exponent(I, keep) -> int:
+    I = _c(I, np.float64); keep = _c(keep, np.uint8)
+    return int(_load().orc_list_exponent(_p(I), _p(keep), I.size))
+
+
+def scale_intensities(I, keep, k):
+    I = _c(I, np.float64); keep = _c(keep, np.uint8)
+    out = np.empty(I.size, np.float32)
+    _load().orc_scale_intensities(_p(I), _p(keep), I.size, int(k), _p(out))
+    return out
+
+
+def sorted_order(nu, keep):
+    """Kept transition indices in ascending (nu bits, index) order."""
+    nu = _c(nu, np.float64); keep = _c(keep, np.uint8)
+    perm = np.empty(nu.size, np.int64)
+    m = _load().orc_sorted_order(_p(nu), _p(keep), nu.size, _p(perm))
+    return perm[:m].copy()
+
+
+def segment_ranges(ilo_sorted, ihi_sorted, n_grid, S):
+    a = _c(ilo_sorted, np.int64); b = _c(ihi_sorted, np.int64)
+    nseg = (n_grid + S - 1) // S
+    first = np.empty(nseg, np.int64); last = np.empty(nseg, np.int64)
+    _load().orc_segment_ranges(_p(a), _p(b), a.size, n_grid, S, _p(first), _p(last))
+    return first, last
+
+
+def widths(kind, nu, gamma_ref, n_T, T, P, mass_da=18.0, hwhm=0.0, T_ref=296.0):
+    nu = _c(nu, np.float64)
+    gr = _c(gamma_ref if gamma_ref is not None else np.zeros(nu.size), np.float32)
+    ne = _c(n_T if n_T is not None else np.zeros(nu.size), np.float32)
+    a = np.empty(nu.size); gm = np.empty(nu.size)
+    _load().orc_widths(KIND[kind], _p(nu), _p(gr), _p(ne), nu.size, T, P, mass_da, hwhm, T_ref, _p(a), _p(gm))
+    return a, gm
+
+
+def cross_section(kind, nu, I, alpha, gamma, keep, ilo, ihi, nu_min, dnu, n_grid):
+    """sigma on the grid (cm^2/molecule), Eq. (xsec)."""
+    nu = _c(np.where(keep.astype(bool), nu, 0.0), np.float64)
+    I = _c(I, np.float64); alpha = _c(alpha, np.float64); gamma = _c(gamma, np.float64)
+    keep = _c(keep, np.uint8); ilo = _c(ilo, np.int64); ihi = _c(ihi, np.int64)
+    sig = np.empty(n_grid)
+    _chk(_load().orc_cross_section(KIND[kind], _p(nu), _p(I), _p(alpha), _p(gamma), _p(keep), _p(ilo), _p(ihi),
+                                   nu.size, nu_min, dnu, n_grid, _p(sig)))
+    return sig
+
+
+def cross_section_grad(kind, E, E_vib, upper, lower, A, nu, I, alpha, gamma, n_T, keep, ilo, ihi,
+                       T, T_vib, P, Qd, nu_min, dnu, w, T_ref=296.0):
+    """Adjoint of L = sum_i w_i sigma_i.  Returns dict of FP64 gradients and scales."""
+    E = _c(E, np.float64); Ev = _c(E_vib, np.float64)
+    up = _c(upper, np.int32); lo = _c(lower, np.int32)
+    A_f32 = A.dtype == np.float32
+    A = _c(A, np.float32 if A_f32 else np.float64)
+    nu = _c(np.where(keep.astype(bool), nu, 1.0), np.float64)
+    I = _c(I, np.float64); alpha = _c(alpha, np.float64); gamma = _c(gamma, np.float64)
+    ne = _c(n_T if n_T is not None else np.zeros(nu.size), np.float32)
+    keep = _c(keep, np.uint8); ilo = _c(ilo, np.int64); ihi = _c(ihi, np.int64)
+    Qd = _c(Qd, np.float64); w = _c(w, np.float64)
+    n = nu.size
+    dA = np.empty(n); dg = np.empty(n); G = np.empty((n, 3)); Gabs = np.empty((n, 3)); scal = np.empty(6)
+    _chk(_load().orc_cross_section_grad(KIND[kind], _p(E), _p(Ev), _p(up), _p(lo), _p(A), int(A_f32),
+                                        _p(nu), _p(I), _p(alpha), _p(gamma), _p(ne), _p(keep), _p(ilo), _p(ihi),
+                                        n, T, T_vib, P, T_ref, _p(Qd), nu_min, dnu, _p(w),
+                                        _p(dA), _p(dg), _p(G), _p(Gabs), _p(scal)))
+    return {"dA": dA, "dgamma_ref": dg, "G": G, "Gabs": Gabs,
+            "dT": scal[0], "dTvib": scal[1], "dP": scal[2],
+            "dT_abs": scal[3], "dTvib_abs": scal[4], "dP_abs": scal[5]}
+
+
+def run(E, g, E_vib, upper, lower, A, gamma_ref, n_T, *, kind, T, T_vib=0.0, P=1.0, mass_da=18.0,
+        hwhm=0.0, nu_min, dnu, n_grid, cut, threshold=0.0, T_ref=296.0, with_sigma=True):
+    """Whole forward path: Q, per-line quantities, exponent, sort order, sigma."""
+    Qd = partition(E, g, E_vib if T_vib > 0 else None, T, T_vib)
+    nu, I, keep, ilo, ihi = line_intensities(E, g, E_vib, upper, lower, A, T, T_vib, Qd[0],
+                                             nu_min, dnu, n_grid, cut, threshold)
+    k = list_exponent(I, keep)
+    I_s = scale_intensities(I, keep, k)
+    perm = sorted_order(nu, keep)
+    nu_w = np.where(keep.astype(bool), nu, 1.0)
+    alpha, gamma = widths(kind, nu_w, gamma_ref, n_T, T, P, mass_da, hwhm, T_ref)
+    out = {"Q": Qd, "nu": nu, "I": I, "keep": keep, "ilo": ilo, "ihi": ihi, "k": k, "I_s": I_s,
+           "perm": perm, "alpha": alpha, "gamma": gamma,
+           "evals": int(np.sum((ihi - ilo + 1)[keep.astype(bool)]))}
+    if with_sigma:
+        out["sigma"] = cross_section(kind, nu, I, alpha, gamma, keep, ilo, ihi, nu_min, dnu, n_grid)
+    return out

@@ -1,0 +1,458 @@
+/*
+ * FP64 CPU ORACLE for line intensities and cross sections (PyExoCross 2.0,
+ * Secs. 2.4.2, 2.4.3, 3.1, 3.2).  TEST INFRASTRUCTURE ONLY: imported by the
+ * tests, by the smoke check and by the CPU-baseline leg of the benchmark, never
+ * by the product path.  It shares no code, header or constant table with the
+ * CUDA library; the only thing both consume is the seeded input data.
+ *
+ * Everything here is the plain definition, written out loop by loop in double
+ * precision, in the paper's order:
+ *   Q(T)                 Eq. (pf):          sum_n g_n exp(-c2 E_n / T)
+ *   Q(T_vib, T_rot)      Eq. (Q nlte 2T):   sum g exp(-c2 E_vib/T_vib) exp(-c2 E_rot/T_rot)
+ *   nu                   Sec. 2.4.3:        E' - E'', lines with nu <= 0 discarded
+ *   I (LTE)              Eq. (abs intensity lte)
+ *   I (two-temperature)  Eqs. (nlte v), (nlte ab 2T)  [brace reading R9 below]
+ *   sigma(nu_i)          Eq. (xsec):        sum_l I_l f_l(nu_i - nu_l), |nu_i - nu_l| <= cut
+ *   profiles             Table (profile): Doppler/Gaussian, Lorentzian, Voigt
+ *   adjoint              analytic derivatives of the above (no counterpart in the paper)
+ *
+ * Readings where the text is silent or garbled (each also listed in the design doc):
+ *   R7  nu = E' - E''; lines with nu <= 0 are dropped (nu = 0 would divide by zero).
+ *   R8  window of grid indices: i_lo = ceil((nu - cut - nu_min)/dnu),
+ *       i_hi = floor((nu + cut - nu_min)/dnu), plain IEEE double, no FMA,
+ *       clamped to the grid; no renormalisation of the truncated profile.
+ *   R9  2T stimulated-emission factor 1 - exp(-c2 (nu_vib/T_vib + nu_rot/T_rot)).
+ *   R10 threshold: keep I >= S_min.
+ *   R11 line order: ascending nu bit pattern, ties by transition index.
+ *   R12 per-list exponent: k = frexp exponent of max kept I; I_s = (float) ldexp(I, -k).
+ *   R15 states with NaN energy are absent: skipped in Q, lines touching them dropped.
+ *   Doppler HWHM alpha = (nu/c) sqrt(2 N_A k_B T ln2 / M) (standard form; the
+ *   formula itself is deferred by the paper to its predecessor).
+ *   Lorentz HWHM gamma = gamma_ref (T_ref/T)^n P, with P used directly in the
+ *   unit of gamma_ref.  In the two-temperature case T_rot sets both widths
+ *   (Sec. 3.3).
+ *
+ * Voigt: V(x) = Re w(z) / (s sqrt(2 pi)), s = alpha / sqrt(2 ln 2),
+ * z = (x + i gamma) / (s sqrt 2), the definition behind scipy.special.voigt_profile
+ * (Table "profile").  w(z) is evaluated by the Laplace continued fraction
+ * (40 levels) for |x| + y >= 8 and by Weideman's rational expansion
+ * (J.A.C. Weideman, SIAM J. Numer. Anal. 31 (1994) 1497, N = 64, coefficients
+ * from the trapezoidal Fourier sum of (L^2 + t^2) exp(-t^2) at t = L tan(theta/2))
+ * elsewhere.  Pinned in the tests against scipy.special.wofz / voigt_profile.
+ *
+ * Status codes: 0 ok, 1 bad argument, 2 state id out of range, 3 non-finite
+ * input, 4 Boltzmann exponent overflow (> 709.78).
+ */
+#include <complex.h>
+#undef I
+#define CI _Complex_I
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* CODATA 2018 exact SI values, in cgs (Table "notation"). */
+#define ORC_H 6.62607015e-27     /* erg s */
+#define ORC_C 2.99792458e10      /* cm / s */
+#define ORC_KB 1.380649e-16      /* erg / K */
+#define ORC_NA 6.02214076e23     /* 1 / mol */
+#define ORC_PI 3.14159265358979323846
+#define ORC_LN2 0.69314718055994530942
+#define ORC_SQRTPI 1.77245385090551602730
+#define ORC_EXP_MAX 709.78
+
+enum { ORC_OK = 0, ORC_ERR_ARG = 1, ORC_ERR_ID = 2, ORC_ERR_NONFINITE = 3, ORC_ERR_OVERFLOW = 4 };
+enum { ORC_GAUSS_DOPPLER = 0, ORC_GAUSS_HWHM = 1, ORC_LORENTZ = 2, ORC_VOIGT = 3 };
+
+double orc_c2(void) { return ORC_H * ORC_C / ORC_KB; }
+
+/* ---------------------------------------------------------------------------
+ * Faddeeva function w(z), Im z >= 0.
+ * ------------------------------------------------------------------------ */
+
+#define WEID_N 64
+static double weid_a[WEID_N + 1];
+static double weid_L;
+
+static void weideman_init(void) {
+  /* f(t) = (L^2 + t^2) exp(-t^2) expanded in powers of Z = e^{i theta},
+   * t = L tan(theta/2); a_n = (1/2pi) int f cos(n theta) dtheta by the
+   * trapezoidal rule on 2M points (f = 0 at theta = +-pi), M = 2N. */
+  const int M = 2 * WEID_N;
+  weid_L = sqrt((double)WEID_N / sqrt(2.0));
+  for (int n = 0; n <= WEID_N; ++n) {
+    double s = 0.0;
+    for (int k = -M + 1; k <= M - 1; ++k) {
+      double th = (double)k * ORC_PI / (double)M;
+      double t = weid_L * tan(0.5 * th);
+      s += exp(-t * t) * (weid_L * weid_L + t * t) * cos((double)n * th);
+    }
+    weid_a[n] = s / (2.0 * (double)M);
+  }
+}
+
+__attribute__((constructor)) static void orc_init(void) { weideman_init(); }
+
+static double complex faddeeva(double x, double y) {
+  double complex z = x + CI * y;
+  if (fabs(x) + y >= 8.0) {
+    /* w(z) = (i/sqrt(pi)) / (z - (1/2)/(z - 1/(z - (3/2)/(z - ...)))) */
+    double complex r = 0.0;
+    for (int k = 40; k >= 1; --k) r = (0.5 * (double)k) / (z - r);
+    return (CI / ORC_SQRTPI) / (z - r);
+  }
+  double complex d = weid_L - CI * z;
+  double complex Z = (weid_L + CI * z) / d;
+  double complex p = 0.0;
+  for (int n = WEID_N; n >= 1; --n) p = p * Z + weid_a[n];
+  return 2.0 * p / (d * d) + (1.0 / ORC_SQRTPI) / d;
+}
+
+void orc_faddeeva(int64_t n, const double* x, const double* y, double* re, double* im) {
+  for (int64_t i = 0; i < n; ++i) {
+    double complex w = faddeeva(x[i], y[i]);
+    re[i] = creal(w);
+    im[i] = cimag(w);
+  }
+}
+
+/* ---------------------------------------------------------------------------
+ * Profiles f(x) with x = nu_i - nu_l, and their width derivatives.
+ * ------------------------------------------------------------------------ */
+
+static double prof_gauss(double x, double a) {
+  return sqrt(ORC_LN2 / ORC_PI) / a * exp(-ORC_LN2 * x * x / (a * a));
+}
+static double prof_lorentz(double x, double g) { return g / (ORC_PI * (x * x + g * g)); }
+static double prof_voigt(double x, double a, double g) {
+  double s = a / sqrt(2.0 * ORC_LN2);
+  double complex w = faddeeva(x / (s * sqrt(2.0)), g / (s * sqrt(2.0)));
+  return creal(w) / (s * sqrt(2.0 * ORC_PI));
+}
+
+/* f, df/dalpha, df/dgamma for one profile kind. */
+static void prof_eval(int kind, double x, double a, double g, double* f, double* fa, double* fg) {
+  if (kind == ORC_GAUSS_DOPPLER || kind == ORC_GAUSS_HWHM) {
+    double v = prof_gauss(x, a);
+    *f = v;
+    *fa = v * (-1.0 / a + 2.0 * ORC_LN2 * x * x / (a * a * a));
+    *fg = 0.0;
+  } else if (kind == ORC_LORENTZ) {
+    double d = x * x + g * g;
+    *f = prof_lorentz(x, g);
+    *fa = 0.0;
+    *fg = (x * x - g * g) / (ORC_PI * d * d);
+  } else {
+    /* V = Re w(z) c / sqrt(pi), c = sqrt(ln2)/alpha = 1/(s sqrt 2), z = (x + i g) c.
+     * w'(z) = -2 z w(z) + 2i/sqrt(pi).
+     * dV/dgamma = -(c^2/sqrt(pi)) Im w'(z);
+     * dV/dalpha = -(c/(alpha sqrt(pi))) (Re w + Re(z w'(z))). */
+    double c = sqrt(ORC_LN2) / a;
+    double complex z = (x + CI * g) * c;
+    double complex w = faddeeva(creal(z), cimag(z));
+    double complex wp = -2.0 * z * w + 2.0 * CI / ORC_SQRTPI;
+    *f = creal(w) * c / ORC_SQRTPI;
+    *fg = -(c * c / ORC_SQRTPI) * cimag(wp);
+    *fa = -(c / (a * ORC_SQRTPI)) * (creal(w) + creal(z * wp));
+  }
+}
+
+void orc_profile(int kind, int64_t n, const double* x, double a, double g, double* f, double* fa, double* fg) {
+  for (int64_t i = 0; i < n; ++i) {
+    double t0, t1, t2;
+    prof_eval(kind, x[i], a, g, &t0, &t1, &t2);
+    f[i] = t0;
+    if (fa) fa[i] = t1;
+    if (fg) fg[i] = t2;
+  }
+}
+
+/* ---------------------------------------------------------------------------
+ * Partition functions, Eqs. (pf) and (Q nlte 2T).  T_vib <= 0 selects LTE.
+ * out[0] = Q, out[1] = dQ/dT (LTE) or dQ/dT_rot (2T), out[2] = dQ/dT_vib (2T).
+ * ------------------------------------------------------------------------ */
+
+int orc_partition(const double* E, const int32_t* g, const double* E_vib, int64_t n,
+                  double T, double T_vib, double* out) {
+  if (!(T > 0.0) || (T_vib > 0.0 && !E_vib)) return ORC_ERR_ARG;
+  const double c2 = orc_c2();
+  double Q = 0.0, dQ = 0.0, dQv = 0.0;
+  for (int64_t s = 0; s < n; ++s) {
+    if (isnan(E[s])) continue;
+    if (!isfinite(E[s])) return ORC_ERR_NONFINITE;
+    if (T_vib > 0.0) {
+      double ev = E_vib[s], er = E[s] - ev;
+      if (!isfinite(ev)) return ORC_ERR_NONFINITE;
+      double xv = -c2 * ev / T_vib, xr = -c2 * er / T;
+      if (xv + xr > ORC_EXP_MAX || xv > ORC_EXP_MAX || xr > ORC_EXP_MAX) return ORC_ERR_OVERFLOW;
+      double term = (double)g[s] * exp(xv) * exp(xr);
+      Q += term;
+      dQ += term * c2 * er / (T * T);
+      dQv += term * c2 * ev / (T_vib * T_vib);
+    } else {
+      double x = -c2 * E[s] / T;
+      if (x > ORC_EXP_MAX) return ORC_ERR_OVERFLOW;
+      double term = (double)g[s] * exp(x);
+      Q += term;
+      dQ += term * c2 * E[s] / (T * T);
+    }
+  }
+  out[0] = Q;
+  out[1] = dQ;
+  out[2] = dQv;
+  return ORC_OK;
+}
+
+/* ---------------------------------------------------------------------------
+ * Per-line quantities.  For every transition t:
+ *   nu[t]  = E[u] - E[l]                       (NaN if a state is absent)
+ *   I[t]   = intensity in cm/molecule (0 where not kept)
+ *   keep[t]= 1 if nu > 0, the cut-off window meets the grid, and I >= S_min
+ *   ilo/ihi= window of grid indices (R8), valid where keep
+ * A is float64 (A_f32 == 0) or float32.
+ * ------------------------------------------------------------------------ */
+
+static int window(double nu, double nu_min, double dnu, int64_t n_grid, double cut,
+                  int64_t* lo, int64_t* hi) {
+  double a = ceil(((nu - cut) - nu_min) / dnu);
+  double b = floor(((nu + cut) - nu_min) / dnu);
+  if (b < 0.0 || a > (double)(n_grid - 1) || a > b) return 0;
+  *lo = a < 0.0 ? 0 : (int64_t)a;
+  *hi = b > (double)(n_grid - 1) ? n_grid - 1 : (int64_t)b;
+  return 1;
+}
+
+int orc_line_intensities(const double* E, const int32_t* g, const double* E_vib, int64_t n_states,
+                         const int32_t* upper, const int32_t* lower, const void* A, int A_f32, int64_t n,
+                         double T, double T_vib, double Q,
+                         double nu_min, double dnu, int64_t n_grid, double cut, double threshold,
+                         double* nu_out, double* I_out, uint8_t* keep, int64_t* ilo, int64_t* ihi) {
+  if (!(T > 0.0) || !(Q > 0.0) || !(dnu > 0.0) || cut < 0.0 || n_grid < 1) return ORC_ERR_ARG;
+  const double c2 = orc_c2();
+  int status = ORC_OK;
+  for (int64_t t = 0; t < n; ++t) {
+    int64_t u = upper[t], l = lower[t];
+    nu_out[t] = NAN; I_out[t] = 0.0; keep[t] = 0; ilo[t] = 0; ihi[t] = -1;
+    if (u < 0 || u >= n_states || l < 0 || l >= n_states) return ORC_ERR_ID;
+    double a = A_f32 ? (double)((const float*)A)[t] : ((const double*)A)[t];
+    if (!isfinite(a)) return ORC_ERR_NONFINITE;
+    double nu = E[u] - E[l];
+    nu_out[t] = nu;
+    if (!(nu > 0.0)) continue;                                  /* R7, R15 */
+    int64_t lo, hi;
+    if (!window(nu, nu_min, dnu, n_grid, cut, &lo, &hi)) continue;
+    double gu = (double)g[u];
+    double pref = gu * a / (8.0 * ORC_PI * ORC_C * nu * nu);
+    double I;
+    if (T_vib > 0.0) {
+      /* Eqs. (nlte v), (nlte ab 2T) */
+      double ev_l = E_vib[l], er_l = E[l] - ev_l;
+      double ev_u = E_vib[u], er_u = E[u] - ev_u;
+      double nu_vib = ev_u - ev_l, nu_rot = er_u - er_l;
+      double xv = -c2 * ev_l / T_vib, xr = -c2 * er_l / T;
+      if (xv > ORC_EXP_MAX || xr > ORC_EXP_MAX || xv + xr > ORC_EXP_MAX) { status = ORC_ERR_OVERFLOW; break; }
+      I = pref * exp(xv) * exp(xr) * (1.0 - exp(-c2 * (nu_vib / T_vib + nu_rot / T))) / Q;
+    } else {
+      /* Eq. (abs intensity lte) */
+      double x = -c2 * E[l] / T;
+      if (x > ORC_EXP_MAX) { status = ORC_ERR_OVERFLOW; break; }
+      I = pref * exp(x) * (1.0 - exp(-c2 * nu / T)) / Q;
+    }
+    if (!(I >= threshold)) continue;                            /* R10 */
+    I_out[t] = I;
+    keep[t] = 1;
+    ilo[t] = lo;
+    ihi[t] = hi;
+  }
+  return status;
+}
+
+/* R12: k = exponent of the largest kept intensity (max = m 2^k, 0.5 <= m < 1). */
+int32_t orc_list_exponent(const double* I, const uint8_t* keep, int64_t n) {
+  double mx = 0.0;
+  for (int64_t t = 0; t < n; ++t)
+    if (keep[t] && I[t] > mx) mx = I[t];
+  if (mx == 0.0) return 0;
+  int k;
+  frexp(mx, &k);
+  return (int32_t)k;
+}
+
+void orc_scale_intensities(const double* I, const uint8_t* keep, int64_t n, int32_t k, float* I_s) {
+  for (int64_t t = 0; t < n; ++t) I_s[t] = keep[t] ? (float)ldexp(I[t], -k) : 0.0f;
+}
+
+/* R11: kept lines in ascending (nu bit pattern, index) order. */
+static const double* g_sort_nu;
+static int cmp_line(const void* pa, const void* pb) {
+  int64_t a = *(const int64_t*)pa, b = *(const int64_t*)pb;
+  uint64_t ka, kb;
+  memcpy(&ka, &g_sort_nu[a], 8);
+  memcpy(&kb, &g_sort_nu[b], 8);
+  if (ka != kb) return ka < kb ? -1 : 1;
+  return a < b ? -1 : (a > b);
+}
+
+int64_t orc_sorted_order(const double* nu, const uint8_t* keep, int64_t n, int64_t* perm) {
+  int64_t m = 0;
+  for (int64_t t = 0; t < n; ++t)
+    if (keep[t]) perm[m++] = t;
+  g_sort_nu = nu;
+  qsort(perm, (size_t)m, sizeof(int64_t), cmp_line);
+  return m;
+}
+
+/* Segment binning: for grid segments [s*S, (s+1)*S), the first sorted line whose
+ * window reaches the segment and one past the last whose window starts in or
+ * before it.  Windows are monotone in nu, so the lines of a segment are
+ * contiguous in sorted order. */
+void orc_segment_ranges(const int64_t* ilo_sorted, const int64_t* ihi_sorted, int64_t m,
+                        int64_t n_grid, int64_t S, int64_t* first, int64_t* last) {
+  int64_t nseg = (n_grid + S - 1) / S;
+  for (int64_t s = 0; s < nseg; ++s) {
+    int64_t a = s * S, b = (s + 1) * S - 1;
+    int64_t f = 0;
+    while (f < m && ihi_sorted[f] < a) ++f;
+    int64_t e = f;
+    while (e < m && ilo_sorted[e] <= b) ++e;
+    first[s] = f;
+    last[s] = e;
+  }
+}
+
+/* ---------------------------------------------------------------------------
+ * Line widths (HWHM) for one condition.
+ * ------------------------------------------------------------------------ */
+
+void orc_widths(int kind, const double* nu, const float* gamma_ref, const float* n_T, int64_t n,
+                double T, double P, double mass_da, double hwhm, double T_ref,
+                double* alpha, double* gamma) {
+  double dop = sqrt(2.0 * ORC_NA * ORC_KB * T * ORC_LN2 / mass_da) / ORC_C;
+  for (int64_t t = 0; t < n; ++t) {
+    alpha[t] = kind == ORC_GAUSS_HWHM ? hwhm : nu[t] * dop;
+    gamma[t] = (kind == ORC_LORENTZ || kind == ORC_VOIGT)
+                   ? (double)gamma_ref[t] * pow(T_ref / T, (double)n_T[t]) * P
+                   : 0.0;
+  }
+}
+
+/* ---------------------------------------------------------------------------
+ * Cross section, Eq. (xsec): sigma_i = sum_l I_l f_l(nu_i - nu_l) over the
+ * window of each kept line.  Grid points nu_i = nu_min + i dnu.  The grid is
+ * split among threads; each point sums its lines in transition-index order.
+ * ------------------------------------------------------------------------ */
+
+int orc_cross_section(int kind, const double* nu, const double* I, const double* alpha, const double* gamma,
+                      const uint8_t* keep, const int64_t* ilo, const int64_t* ihi, int64_t n,
+                      double nu_min, double dnu, int64_t n_grid, double* sigma) {
+  for (int64_t i = 0; i < n_grid; ++i) sigma[i] = 0.0;
+  int64_t nblk = 256;
+  int64_t bs = (n_grid + nblk - 1) / nblk;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t b = 0; b < nblk; ++b) {
+    int64_t a0 = b * bs, a1 = a0 + bs - 1;
+    if (a1 > n_grid - 1) a1 = n_grid - 1;
+    if (a0 > a1) continue;
+    for (int64_t t = 0; t < n; ++t) {
+      if (!keep[t] || ihi[t] < a0 || ilo[t] > a1) continue;
+      int64_t lo = ilo[t] > a0 ? ilo[t] : a0, hi = ihi[t] < a1 ? ihi[t] : a1;
+      for (int64_t i = lo; i <= hi; ++i) {
+        double x = (nu_min + (double)i * dnu) - nu[t];
+        double f;
+        if (kind == ORC_LORENTZ) f = prof_lorentz(x, gamma[t]);
+        else if (kind == ORC_VOIGT) f = prof_voigt(x, alpha[t], gamma[t]);
+        else f = prof_gauss(x, alpha[t]);
+        sigma[i] += I[t] * f;
+      }
+    }
+  }
+  return ORC_OK;
+}
+
+/* ---------------------------------------------------------------------------
+ * Adjoint of L = sum_i w_i sigma_i (no counterpart in the paper).
+ * Per kept line l, with f_li = f_l(nu_i - nu_l):
+ *   G_l = sum_i w_i f_li,  Da_l = sum_i w_i df/dalpha,  Dg_l = sum_i w_i df/dgamma
+ * and the absolute sums (|w| in place of w) that set the scale of each.
+ *   dL/dA_l        = (I_l / A_l) G_l
+ *   dL/dgamma_ref_l = I_l (T_ref/T)^n P Dg_l
+ *   dL/dP          = sum_l I_l (gamma_l / P) Dg_l
+ *   dL/dT (LTE) or dL/dT_rot (2T)
+ *                  = sum_l I_l [ dlnI/dT G_l + (alpha_l / 2T) Da_l - (n_l gamma_l / T) Dg_l ]
+ *   dL/dT_vib      = sum_l I_l dlnI/dT_vib G_l
+ * with
+ *   LTE: dlnI/dT = c2 E''/T^2 - (c2 nu/T^2) e^{-c2 nu/T}/(1 - e^{-c2 nu/T}) - Q'/Q
+ *   2T : dlnI/dT_rot = c2 E''_rot/T_rot^2 - (c2 nu_rot/T_rot^2) e^{-X}/(1-e^{-X}) - Q_rot'/Q
+ *        dlnI/dT_vib = c2 E''_vib/T_vib^2 - (c2 nu_vib/T_vib^2) e^{-X}/(1-e^{-X}) - Q_vib'/Q
+ *        X = c2 (nu_vib/T_vib + nu_rot/T_rot).
+ * (For the Gaussian-HWHM profile alpha does not depend on T.)
+ * scal[0..2] = dL/dT, dL/dT_vib, dL/dP; scal[3..5] = the same with absolute values.
+ * ------------------------------------------------------------------------ */
+
+int orc_cross_section_grad(int kind, const double* E, const double* E_vib,
+                           const int32_t* upper, const int32_t* lower, const void* A, int A_f32,
+                           const double* nu, const double* I, const double* alpha, const double* gamma,
+                           const float* n_T, const uint8_t* keep, const int64_t* ilo, const int64_t* ihi,
+                           int64_t n, double T, double T_vib, double P, double T_ref, const double* Qd,
+                           double nu_min, double dnu, const double* w,
+                           double* dA, double* dgref, double* G, double* Gabs, double* scal) {
+  const double c2 = orc_c2();
+  double* cT = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  double* cTv = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  double* cP = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  double* aT = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  double* aTv = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  double* aP = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t t = 0; t < n; ++t) {
+    dA[t] = 0.0; dgref[t] = 0.0; G[3 * t] = G[3 * t + 1] = G[3 * t + 2] = 0.0;
+    Gabs[3 * t] = Gabs[3 * t + 1] = Gabs[3 * t + 2] = 0.0;
+    if (!keep[t]) continue;
+    double g0 = 0, ga = 0, gg = 0, h0 = 0, ha = 0, hg = 0;
+    for (int64_t i = ilo[t]; i <= ihi[t]; ++i) {
+      double x = (nu_min + (double)i * dnu) - nu[t];
+      double f, fa, fg;
+      prof_eval(kind, x, alpha[t], gamma[t], &f, &fa, &fg);
+      g0 += w[i] * f; ga += w[i] * fa; gg += w[i] * fg;
+      h0 += fabs(w[i] * f); ha += fabs(w[i] * fa); hg += fabs(w[i] * fg);
+    }
+    G[3 * t] = g0; G[3 * t + 1] = ga; G[3 * t + 2] = gg;
+    Gabs[3 * t] = h0; Gabs[3 * t + 1] = ha; Gabs[3 * t + 2] = hg;
+    double a = A_f32 ? (double)((const float*)A)[t] : ((const double*)A)[t];
+    double Il = I[t];
+    dA[t] = Il / a * g0;
+    double dgam_dgref = (kind == ORC_LORENTZ || kind == ORC_VOIGT) ? pow(T_ref / T, (double)n_T[t]) * P : 0.0;
+    dgref[t] = Il * dgam_dgref * gg;
+    int64_t u = upper[t], l = lower[t];
+    double dlnT, dlnTv = 0.0;
+    if (T_vib > 0.0) {
+      double ev_l = E_vib[l], er_l = E[l] - ev_l, ev_u = E_vib[u], er_u = E[u] - ev_u;
+      double nv = ev_u - ev_l, nr = er_u - er_l;
+      double X = c2 * (nv / T_vib + nr / T);
+      double st = exp(-X) / (1.0 - exp(-X));
+      dlnT = c2 * er_l / (T * T) - c2 * nr / (T * T) * st - Qd[1] / Qd[0];
+      dlnTv = c2 * ev_l / (T_vib * T_vib) - c2 * nv / (T_vib * T_vib) * st - Qd[2] / Qd[0];
+    } else {
+      double X = c2 * nu[t] / T;
+      double st = exp(-X) / (1.0 - exp(-X));
+      dlnT = c2 * E[l] / (T * T) - c2 * nu[t] / (T * T) * st - Qd[1] / Qd[0];
+    }
+    double dalpha_dT = (kind == ORC_GAUSS_DOPPLER || kind == ORC_VOIGT) ? alpha[t] / (2.0 * T) : 0.0;
+    double dgamma_dT = (kind == ORC_LORENTZ || kind == ORC_VOIGT) ? -(double)n_T[t] * gamma[t] / T : 0.0;
+    double dgamma_dP = (kind == ORC_LORENTZ || kind == ORC_VOIGT) ? gamma[t] / P : 0.0;
+    cT[t] = Il * (dlnT * g0 + dalpha_dT * ga + dgamma_dT * gg);
+    cTv[t] = Il * dlnTv * g0;
+    cP[t] = Il * dgamma_dP * gg;
+    aT[t] = Il * (fabs(dlnT) * h0 + fabs(dalpha_dT) * ha + fabs(dgamma_dT) * hg);
+    aTv[t] = Il * fabs(dlnTv) * h0;
+    aP[t] = Il * fabs(dgamma_dP) * hg;
+  }
+  double s[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t t = 0; t < n; ++t) {
+    s[0] += cT[t]; s[1] += cTv[t]; s[2] += cP[t];
+    s[3] += aT[t]; s[4] += aTv[t]; s[5] += aP[t];
+  }
+  for (int j = 0; j < 6; ++j) scal[j] = s[j];
+  free(cT); free(cTv); free(cP); free(aT); free(aTv); free(aP);
+  return ORC_OK;
+}
