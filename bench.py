@@ -1,0 +1,474 @@
+#!/usr/bin/env python3
+"""Benchmark of the line-list -> cross-section hot path on B300.
+
+Headline: Voigt line-grid evals/s (and lines/s) on the 1e9-line workload
+(5e7 polyatomic states, 1e9 transitions in 1e8-line chunks, T = 2000 K,
+P = 0.1 bar, grid 0-30000 cm^-1 at 0.01 cm^-1, cut-off 25 cm^-1, intensity
+threshold 1e-30 cm/molecule).  One step = one full pass of the hot path over
+all 1e9 lines (partition function, intensities, compaction, exact nu sort,
+binning, Voigt accumulation).  Inputs are synthetic and seeded.
+
+  value : device-resident inputs, CUDA events around K steps, max over ranks
+  e2e   : the same through pxc_cross_section_streamed from pinned host arrays
+          (host->device copies of every step inside the timed region) plus the
+          device->host read of sigma
+  extras: the batched 200-condition opacity table against 200 sequential calls,
+          and forward+backward against forward on the two-temperature list
+
+`--impl reference` times the FP64 oracle (the reference arm of this build) on
+bounded samples of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Voigt line-grid evals/s & lines/s at 1e9 lines; batched, fwd+bwd vs plain"
+UNIT = "line-grid evals/s"
+EVAL_FP32_OPS = 6      # FP32-pipe instructions of one region-I Voigt evaluation (fast path)
+L2_BYTES = 126 * 2 ** 20
+
+# DRAM traffic per profile-kernel launch from the committed ncu capture, valid only for
+# the kernel source it was taken on (sha256 prefix of kernels_profile.cu).
+NCU_TRAFFIC = {}
+
+
+def _src_hash(rel):
+    with open(os.path.join(ROOT, rel), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9:
+                self.rows.append(p)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = self.rows
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ----------------------------------------------------------------------------- reference arm (oracle)
+
+def oracle_sample_rate(w, E, g, n_lines, threads):
+    """Oracle throughput (evals/s) on the first n_lines transitions of the workload, full grid."""
+    import numpy as np
+    import oracle
+    up, lo, A = w.transitions(0, n_lines)
+    gr, ne = w.broadening(0, n_lines)
+    t0 = time.perf_counter()
+    r = oracle.run(E, g, None, up, lo, A, gr, ne, kind=w.profile, T=w.T, P=w.P, mass_da=w.mass_da,
+                   nu_min=w.nu_min, dnu=w.dnu, n_grid=w.n_grid, cut=w.cutoff, threshold=w.threshold)
+    dt = time.perf_counter() - t0
+    nz = r["keep"].astype(bool) & (r["I_s"] != 0)
+    evals = int(np.sum((r["ihi"] - r["ilo"] + 1)[nz]))
+    return evals, n_lines, dt
+
+
+def calibrate_sample(w, E, g, threads, target_s):
+    n0 = 200_000
+    ev, n, dt = oracle_sample_rate(w, E, g, n0, threads)
+    n1 = int(min(max(n0 * target_s / max(dt, 1e-3), n0), 5e7))
+    return n1
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import synth
+    w = synth.workload(args.workload)
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    E, g, _ = w.states()
+    n = calibrate_sample(w, E, g, threads, args.ref_step_s)
+    for _ in range(args.warmup):
+        oracle_sample_rate(w, E, g, n, threads)
+    tot_ev, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        ev, _, dt = oracle_sample_rate(w, E, g, n, threads)
+        tot_ev += ev
+        tot_t += dt
+    val = tot_ev / tot_t
+    sample = f"first {n} of {w.n_trans} transitions per step, full grid (oracle FP64, {threads} threads)"
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": w.name, "lines": w.n_trans, "states": w.n_states,
+                                            "grid": w.n_grid, "profile": w.profile},
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def main_pxc(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import paper_2609_17273_b300 as pxc
+    import synth
+
+    rank, world, local = dist_env()
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pxc.load()
+
+    w = synth.workload(args.workload)
+    if args.lines:
+        w = w.scaled(n_trans=args.lines)
+    chunk = w.chunk or w.n_trans
+    nchunks = (w.n_trans + chunk - 1) // chunk
+    E, g, _ = w.states()
+    states = pxc.States(torch.from_numpy(E).to(dev), torch.from_numpy(g).to(dev), None)
+
+    # host (pinned) and device copies of the transition list
+    a_dtype = torch.float32 if w.A_f32 else torch.float64
+    t_gen = time.perf_counter()
+    pin = not args.no_e2e
+    h_up = torch.empty(w.n_trans, dtype=torch.int32, pin_memory=pin)
+    h_lo = torch.empty(w.n_trans, dtype=torch.int32, pin_memory=pin)
+    h_A = torch.empty(w.n_trans, dtype=a_dtype, pin_memory=pin)
+    h_gr = torch.empty(w.n_trans, dtype=torch.float32, pin_memory=pin)
+    h_ne = torch.empty(w.n_trans, dtype=torch.float32, pin_memory=pin)
+    d_up = torch.empty(w.n_trans, dtype=torch.int32, device=dev)
+    d_lo = torch.empty_like(d_up)
+    d_A = torch.empty(w.n_trans, dtype=a_dtype, device=dev)
+    d_gr = torch.empty(w.n_trans, dtype=torch.float32, device=dev)
+    d_ne = torch.empty_like(d_gr)
+    for c in range(nchunks):
+        t0, n = c * chunk, min(chunk, w.n_trans - c * chunk)
+        sl = slice(t0, t0 + n)
+        w.transitions(t0, n, out=(h_up[sl].numpy(), h_lo[sl].numpy(), h_A[sl].numpy()))
+        gr, ne = w.broadening(t0, n)
+        h_gr[sl].numpy()[:] = gr
+        h_ne[sl].numpy()[:] = ne
+        for d, h in ((d_up, h_up), (d_lo, h_lo), (d_A, h_A), (d_gr, h_gr), (d_ne, h_ne)):
+            d[sl].copy_(h[sl], non_blocking=False)
+    t_gen = time.perf_counter() - t_gen
+
+    ws = pxc.Workspace(max_states=w.n_states, max_lines=chunk, max_grid=w.n_grid, device=dev)
+    grid = (w.nu_min, w.dnu, w.n_grid)
+    cond = (w.T, w.T_vib, w.P)
+    sigma = torch.empty(w.n_grid, dtype=torch.float32, device=dev)
+    sexp = torch.empty(1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        ws.set_accumulate(True)
+        sigma.zero_()
+        sexp.fill_(pxc.PXC_EXP_EMPTY)
+        for c in range(nchunks):
+            t0, n = c * chunk, min(chunk, w.n_trans - c * chunk)
+            sl = slice(t0, t0 + n)
+            tr = pxc.Transitions(d_up[sl], d_lo[sl], d_A[sl])
+            prof = pxc.Profile(w.profile, w.cutoff, w.mass_da, w.hwhm, d_gr[sl], d_ne[sl])
+            pxc.pxc_cross_section(ws, states, tr, cond, grid, prof, w.threshold, sigma=sigma.view(1, -1),
+                                  sigma_exp=sexp)
+        ws.set_accumulate(False)
+
+    # one counted step: algorithmic eval counts per chunk
+    ws.set_accumulate(True)
+    sigma.zero_(); sexp.fill_(pxc.PXC_EXP_EMPTY)
+    evals = evals_window = kept = 0
+    for c in range(nchunks):
+        t0, n = c * chunk, min(chunk, w.n_trans - c * chunk)
+        sl = slice(t0, t0 + n)
+        tr = pxc.Transitions(d_up[sl], d_lo[sl], d_A[sl])
+        prof = pxc.Profile(w.profile, w.cutoff, w.mass_da, w.hwhm, d_gr[sl], d_ne[sl])
+        pxc.pxc_cross_section(ws, states, tr, cond, grid, prof, w.threshold, sigma=sigma.view(1, -1), sigma_exp=sexp)
+        s = ws.stats()
+        evals += s["evals_nonzero"]; evals_window += s["evals_window"]; kept += s["n_kept"]
+    ws.set_accumulate(False)
+    ws.sync()
+
+    for _ in range(args.warmup):
+        step()
+    ws.sync()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    clocks = Clocks(local)
+    ws.set_timing(True)
+    launches0 = pxc.kernel_launches()
+    barrier()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    launches = pxc.kernel_launches() - launches0
+    ms = ev0.elapsed_time(ev1)
+    tm = ws.timing()
+    ws.set_timing(False)
+    ws.sync()
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = world * evals * args.steps / (ms_max / 1e3)
+    lines_per_s = world * w.n_trans * args.steps / (ms_max / 1e3)
+
+    # ---------------------------------------------------------------- e2e through the host-streaming ABI call
+    e2e = None
+    if not args.no_e2e:
+        bufs = None
+        h_sig = torch.empty(w.n_grid, dtype=torch.float32, pin_memory=True)
+        h_exp = torch.empty(1, dtype=torch.int32, pin_memory=True)
+        prof0 = pxc.Profile(w.profile, w.cutoff, w.mass_da, w.hwhm, None, None)
+
+        def step_e2e(bufs):
+            sig, e, bufs = pxc.pxc_cross_section_streamed(ws, states, h_up, h_lo, h_A, h_gr, h_ne, cond, grid, prof0,
+                                                          w.threshold, bufs=bufs, sigma=sigma, sigma_exp=sexp)
+            h_sig.copy_(sig, non_blocking=True)
+            h_exp.copy_(e, non_blocking=True)
+            return bufs
+
+        bufs = step_e2e(bufs)
+        ws.sync()
+        n_e2e = max(1, min(args.steps, 3))
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n_e2e):
+            bufs = step_e2e(bufs)
+        e1.record(stream)
+        barrier()
+        ms_e = e0.elapsed_time(e1)
+        mt = torch.tensor([ms_e], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(mt, op=dist.ReduceOp.MAX)
+        ms_e = float(mt.item())
+        h2d = w.n_trans * (4 + 4 + (4 if w.A_f32 else 8) + 8)
+        e2e = {"value": world * evals * n_e2e / (ms_e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": w.n_grid * 4 + 4, "steps": n_e2e, "ms_per_step": ms_e / n_e2e,
+               "lines_per_s": world * w.n_trans * n_e2e / (ms_e / 1e3)}
+
+    # ---------------------------------------------------------------- rooflines
+    peaks, peak_src = _peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    sm_max = float(clk.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2032.0))
+    alu_peak = sms * 128 * sm_max * 1e6 / 1e12            # T FP32 lane-ops/s
+    prof_ms, prof_n = tm["profile"]
+    int_ms, int_n = tm["intensity"]
+    sort_ms, sort_n = tm["sort"]
+    per_launch_ops = EVAL_FP32_OPS * evals / nchunks
+    prof_launch_ms = prof_ms / max(prof_n, 1)
+    ach_alu = per_launch_ops / (prof_launch_ms / 1e3) / 1e12
+    per_launch_bytes = (chunk * (4 + 4 + (4 if w.A_f32 else 8)) + chunk * (8 + 8))
+    int_launch_ms = int_ms / max(int_n, 1)
+    ach_hbm = per_launch_bytes / (int_launch_ms / 1e3) / 1e9
+    kvh = _src_hash("paper_2609_17273_b300/csrc/kernels_profile.cu")
+    klh = _src_hash("paper_2609_17273_b300/csrc/kernels_lines.cu")
+    tr_prof = NCU_TRAFFIC.get(("profile", kvh))
+    tr_int = NCU_TRAFFIC.get(("intensity", klh))
+    roof_profile = {"bound": "alu", "achieved": ach_alu, "peak": alu_peak, "unit": "T FP32 lane-ops/s",
+                    "frac": ach_alu / alu_peak, "traffic": tr_prof, "kernel": "k_profile<VOIGT>",
+                    "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz",
+                    "ops_per_eval": EVAL_FP32_OPS, "launch_ms": prof_launch_ms}
+    roof_int = {"bound": "hbm", "achieved": ach_hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach_hbm / peaks["hbm_gbs"], "traffic": tr_int, "kernel": "k_lines",
+                "peak_source": f"hbm_gbs of {peak_src}", "bytes_per_line": per_launch_bytes / chunk,
+                "launch_ms": int_launch_ms}
+    dominant = roof_profile if prof_ms >= int_ms else roof_int
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": w.name, "lines": w.n_trans, "states": w.n_states, "grid": w.n_grid,
+                      "chunk": chunk, "profile": w.profile, "T": w.T, "P": w.P, "cutoff": w.cutoff,
+                      "threshold": w.threshold, "parallelism": f"replicas x{world}",
+                      "l2": "inputs (20 GB) larger than L2", "fp64": "nu, Boltzmann factors, Q"},
+           "lines_per_s": lines_per_s,
+           "counts": {"kept_lines": kept, "evals_nonzero": evals, "evals_window": evals_window},
+           "pass_ms_per_step": {"intensity": int_ms / args.steps, "sort": sort_ms / args.steps,
+                                "profile": prof_ms / args.steps},
+           "roofline": dominant, "rooflines": {"profile": roof_profile, "intensity": roof_int},
+           "gpu_launches": launches, "clocks": clk, "e2e": e2e, "setup_s": t_gen}
+
+    if rank == 0 and not args.no_extras:
+        out["extras"] = run_extras(args, pxc, torch, dev, synth)
+    if rank == 0 and not args.no_cpu_baseline:
+        threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        n = calibrate_sample(w, E, g, threads, args.ref_step_s)
+        ev, nl, dt = oracle_sample_rate(w, E, g, n, threads)
+        out["cpu_baseline"] = {"value": ev / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+                               "sample": f"first {nl} of {w.n_trans} transitions, full grid, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def run_extras(args, pxc, torch, dev, synth):
+    """Batched (T, P) table vs sequential plain calls; forward+backward vs forward."""
+    res = {}
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps=1):
+        fn()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / reps
+
+    # batched opacity table
+    w = synth.workload("table_1e8")
+    if args.extras_lines:
+        w = w.scaled(n_trans=args.extras_lines)
+    E, g, _ = w.states()
+    up, lo, A = w.transitions()
+    gr, ne = w.broadening()
+    st = pxc.States(torch.from_numpy(E).to(dev), torch.from_numpy(g).to(dev), None)
+    tr = pxc.Transitions(torch.from_numpy(up).to(dev), torch.from_numpy(lo).to(dev), torch.from_numpy(A).to(dev))
+    prof = pxc.Profile("voigt", w.cutoff, w.mass_da, 0.0, torch.from_numpy(gr).to(dev), torch.from_numpy(ne).to(dev))
+    grid = (w.nu_min, w.dnu, w.n_grid)
+    conds = [(T, 0.0, P) for T, P in w.conditions]
+    nT = len({c[0] for c in conds})
+    wsb = pxc.Workspace(max_states=w.n_states, max_lines=w.n_trans, max_grid=w.n_grid, max_conditions=len(conds),
+                        max_temperatures=nT, device=dev)
+    sig = torch.empty(len(conds), w.n_grid, dtype=torch.float32, device=dev)
+    se = torch.empty(len(conds), dtype=torch.int32, device=dev)
+    ms_b = timed(lambda: pxc.pxc_cross_section(wsb, st, tr, conds, grid, prof, 0.0, sigma=sig, sigma_exp=se))
+    sb = wsb.stats()
+    del wsb
+    wsp = pxc.Workspace(max_states=w.n_states, max_lines=w.n_trans, max_grid=w.n_grid, device=dev)
+    s1 = torch.empty(1, w.n_grid, dtype=torch.float32, device=dev)
+    e1 = torch.empty(1, dtype=torch.int32, device=dev)
+    worst = 0.0
+
+    def seq():
+        for c in conds:
+            pxc.pxc_cross_section(wsp, st, tr, c, grid, prof, 0.0, sigma=s1, sigma_exp=e1)
+
+    ms_s = timed(seq)
+    for i in (0, len(conds) // 2, len(conds) - 1):
+        pxc.pxc_cross_section(wsp, st, tr, conds[i], grid, prof, 0.0, sigma=s1, sigma_exp=e1)
+        a = torch.ldexp(sig[i].double(), se[i].double())
+        b = torch.ldexp(s1[0].double(), e1[0].double())
+        worst = max(worst, float((a - b).abs().max() / b.abs().max().clamp_min(1e-300)))
+    res["batched_table"] = {"workload": w.name, "conditions": len(conds), "lines": w.n_trans,
+                            "batched_ms": ms_b, "sequential_ms": ms_s, "speedup": ms_s / ms_b,
+                            "max_abs_diff_rel_peak": worst, "kept_lines": sb["n_kept"]}
+    del wsp, st, tr, prof, sig
+    torch.cuda.empty_cache()
+
+    # forward + backward on the two-temperature list
+    w = synth.workload("nlte_1e7")
+    E, g, Ev = w.states()
+    up, lo, A = w.transitions()
+    gr, ne = w.broadening()
+    st = pxc.States(torch.from_numpy(E).to(dev), torch.from_numpy(g).to(dev), torch.from_numpy(Ev).to(dev))
+    tr = pxc.Transitions(torch.from_numpy(up).to(dev), torch.from_numpy(lo).to(dev), torch.from_numpy(A).to(dev))
+    prof = pxc.Profile("voigt", w.cutoff, w.mass_da, 0.0, torch.from_numpy(gr).to(dev), torch.from_numpy(ne).to(dev))
+    grid = (w.nu_min, w.dnu, w.n_grid)
+    cond = (w.T, w.T_vib, w.P)
+    wt = torch.from_numpy(w.weights()).to(dev)
+    wsf = pxc.Workspace(max_states=w.n_states, max_lines=w.n_trans, max_grid=w.n_grid, device=dev)
+    ms_f = timed(lambda: pxc.pxc_cross_section(wsf, st, tr, cond, grid, prof), reps=3)
+
+    def fb():
+        pxc.pxc_cross_section(wsf, st, tr, cond, grid, prof)
+        pxc.pxc_cross_section_backward(wsf, st, tr, cond, grid, prof, wt)
+
+    ms_fb = timed(fb, reps=3)
+    res["fwd_bwd"] = {"workload": w.name, "lines": w.n_trans, "fwd_ms": ms_f, "fwd_bwd_ms": ms_fb,
+                      "ratio": ms_fb / ms_f}
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["pxc", "reference"], default="pxc")
+    ap.add_argument("--workload", default="voigt_1e9")
+    ap.add_argument("--lines", type=int, default=0, help="override the transition count (smaller runs)")
+    ap.add_argument("--extras-lines", type=int, default=0, help="override the batched-table transition count")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-step-s", type=float, default=10.0, help="seconds of oracle work per reference step")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return main_pxc(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

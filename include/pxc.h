@@ -1,0 +1,261 @@
+/*
+ * pxc: line-list -> line intensities -> cross sections on one B300 (sm_103a).
+ *
+ * C ABI of the hot path of PyExoCross 2.0 (Zhang, Yurchenko, Tennyson):
+ * partition functions (Sec. 2.4.2, Eq. pf; Sec. 3.1, Eq. Q nlte 2T), LTE and
+ * two-temperature absorption intensities (Sec. 3.2, Eqs. abs intensity lte,
+ * nlte v, nlte ab 2T), and cross sections on a wavenumber grid with a line-wing
+ * cut-off (Sec. 2.4.3, Eq. xsec; Table profile: Doppler/Gaussian, Lorentzian,
+ * Voigt), plus the adjoint of a linear functional of the cross section.
+ *
+ * Conventions shared by every call
+ *  - Every array argument is a DEVICE pointer owned by the caller, unless the
+ *    name says "host".  The library never frees caller memory.
+ *  - The library allocates no device memory after pxc_workspace_create: all
+ *    scratch lives in the caller-provided buffer given to pxc_workspace_create
+ *    (size from pxc_workspace_query).  A workspace is not thread-safe; use one
+ *    workspace per concurrent stream.
+ *  - Calls are asynchronous on `stream` and return a pxc_status describing the
+ *    host-side checks and launch errors.  Errors found by the kernels (bad state
+ *    id, non-finite input, exponent overflow, a bounded wait that ran out) are
+ *    latched in the workspace and returned by pxc_sync_status (which
+ *    synchronises the stream) or pxc_get_stats.  Results of a call that latched
+ *    an error are unspecified.
+ *  - No exception crosses the ABI.  pxc_last_error() gives a thread-local
+ *    message for the last non-OK status returned on the calling thread.
+ *  - Units: energies and wavenumbers in cm^-1, A in s^-1, T in K, P in bar,
+ *    gamma_ref in cm^-1 per unit of P, mass in Da; intensities in cm/molecule,
+ *    cross sections in cm^2/molecule.
+ *  - State ids are 0-based and dense: transition t connects upper[t] and
+ *    lower[t], both in [0, states.n).
+ *  - Scaled results: intensities and cross sections are returned in FP32
+ *    scaled by a per-list power of two, value = stored * 2^exp, so that lists
+ *    whose lines are ~1e-50 neither underflow nor vanish.
+ */
+#ifndef PXC_H
+#define PXC_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PXC_OK = 0,
+  PXC_ERR_ARG = 1,        /* null pointer, n < 0, dnu <= 0, T <= 0, cutoff < 0, ... */
+  PXC_ERR_ID_RANGE = 2,   /* a state id outside [0, states.n) */
+  PXC_ERR_NONFINITE = 3,  /* an infinite energy or a non-finite A */
+  PXC_ERR_OVERFLOW = 4,   /* a Boltzmann exponent above 709.78 (negative energy at low T) */
+  PXC_ERR_TIMEOUT = 5,    /* a bounded device wait ran out; the kernel returned early */
+  PXC_ERR_CUDA = 6,       /* a CUDA launch or runtime error */
+  PXC_ERR_CAPACITY = 7    /* the call exceeds the capacity the workspace was sized for */
+} pxc_status;
+
+/* States (Sec. 2.3, .states file): energy term values E, total degeneracies g,
+ * and, for two-temperature non-LTE, the vibrational part E_vib of each energy
+ * (Eq. Enonlte; E_rot = E - E_vib, Eq. Erot nonlte).  E_vib may be NULL for LTE.
+ * A state whose E is NaN is absent: it adds nothing to Q and its lines are dropped. */
+typedef struct {
+  const double* E;       /* [n] cm^-1 */
+  const int32_t* g;      /* [n] total degeneracy */
+  const double* E_vib;   /* [n] cm^-1, or NULL */
+  int64_t n;
+} pxc_states;
+
+/* Transitions (Sec. 2.3, .trans file): upper id, lower id, Einstein A.
+ * A is float64 unless A_is_f32 != 0 (then float32). */
+typedef struct {
+  const int32_t* upper;  /* [n] */
+  const int32_t* lower;  /* [n] */
+  const void* A;         /* [n] s^-1 */
+  int32_t A_is_f32;
+  int64_t n;
+} pxc_transitions;
+
+/* One thermodynamic condition.  T_vib <= 0 selects LTE at temperature T
+ * (Eq. F lte); T_vib > 0 selects the two-temperature Treanor populations
+ * (Eq. F nlte 2T) with T_rot = T, and T_rot then also sets the Doppler and
+ * pressure widths (Sec. 3.3). */
+typedef struct {
+  double T;
+  double T_vib;
+  double P;              /* bar */
+} pxc_condition;
+
+/* Wavenumber grid nu_i = nu_min + i * dnu, i = 0 .. n-1 (Sec. 2.4.3). */
+typedef struct {
+  double nu_min;
+  double dnu;
+  int64_t n;
+} pxc_grid;
+
+/* Line profiles (Table profile). */
+typedef enum {
+  PXC_GAUSS_DOPPLER = 0, /* Doppler HWHM alpha = (nu/c) sqrt(2 N_A k_B T ln2 / M) */
+  PXC_GAUSS_HWHM = 1,    /* Gaussian with the fixed HWHM `hwhm` */
+  PXC_LORENTZ = 2,       /* gamma = gamma_ref (T_ref/T)^n_T P */
+  PXC_VOIGT = 3          /* Voigt of the Doppler alpha and the Lorentz gamma */
+} pxc_profile;
+
+typedef struct {
+  int32_t kind;          /* pxc_profile */
+  double cutoff;         /* line-wing cut-off: points with |nu_i - nu_l| <= cutoff */
+  double mass_da;        /* molecular mass (Doppler widths) */
+  double hwhm;           /* PXC_GAUSS_HWHM only */
+  const float* gamma_ref;/* [transitions.n] (Lorentz, Voigt), else NULL */
+  const float* n_T;      /* [transitions.n] temperature exponents (Lorentz, Voigt) */
+  double T_ref;          /* reference temperature of gamma_ref, normally 296 K */
+} pxc_profile_args;
+
+/* Capacity a workspace is sized for. */
+typedef struct {
+  int64_t max_states;
+  int64_t max_lines;       /* transitions per call (per chunk when streaming) */
+  int64_t max_grid;
+  int32_t max_conditions;  /* conditions per batched call */
+  int32_t max_temperatures;/* distinct (T, T_vib) pairs per batched call; 0 means max_conditions */
+} pxc_capacity;
+
+typedef struct pxc_workspace pxc_workspace;
+
+/* Bytes of device scratch a workspace of this capacity needs. */
+pxc_status pxc_workspace_query(const pxc_capacity* cap, size_t* bytes);
+
+/* Bind a workspace to `device_scratch` (device memory of at least the queried
+ * size, 256-byte aligned, owned by the caller and kept alive until destroy).
+ * The handle itself is host memory owned by the library. */
+pxc_status pxc_workspace_create(const pxc_capacity* cap, void* device_scratch, size_t bytes,
+                                pxc_workspace** ws);
+pxc_status pxc_workspace_destroy(pxc_workspace* ws);
+
+/* Synchronise `stream`, return and clear the latched device error. */
+pxc_status pxc_sync_status(pxc_workspace* ws, cudaStream_t stream);
+
+/* Thread-local message for the last non-OK status. */
+const char* pxc_last_error(void);
+
+/* Number of CUDA kernels this library has launched since it was loaded (all
+ * workspaces and threads); differences around a region count its launches. */
+int64_t pxc_kernel_launches(void);
+
+/* Accumulate mode (streaming a line list in chunks, Sec. 2.1 and 4: bounded
+ * memory over large .trans files).  When on, pxc_cross_section ADDS the chunk's
+ * lines to sigma_out, whose current exponent is read from sigma_exp_out
+ * (initialise it to PXC_EXP_EMPTY before the first chunk); if a chunk raises
+ * the exponent the existing sum is rescaled on the device.  The partition
+ * function is computed on the first chunk and reused while accumulating, so
+ * the states must not change between chunks. */
+#define PXC_EXP_EMPTY (-2147483647 - 1)
+pxc_status pxc_set_accumulate(pxc_workspace* ws, int on);
+
+/* Partition functions, Eq. (pf) (LTE) or Eq. (Q nlte 2T) (T_vib > 0), summed in
+ * FP64 over all states for each of the n_c conditions.
+ * Q_out:  [n_c] device.
+ * dQ_out: [n_c][2] device, or NULL: dQ/dT (LTE) or dQ/dT_rot, and dQ/dT_vib.
+ * Errors: PXC_ERR_OVERFLOW if some exponent exceeds 709.78, PXC_ERR_NONFINITE
+ * for an infinite energy (latched). */
+pxc_status pxc_partition_function(pxc_workspace* ws, const pxc_states* states,
+                                  const pxc_condition* c, int32_t n_c,
+                                  double* Q_out, double* dQ_out, cudaStream_t stream);
+
+/* Stick spectrum (Sec. 2.4.3, "Stick spectra"): per transition t
+ *   nu_out[t]       = E[upper] - E[lower] (FP64, bit-exact IEEE subtraction)
+ *   I_scaled_out[t] = I_t * 2^-k in FP32, I_t by Eq. (abs intensity lte) or
+ *                     Eq. (nlte ab 2T); 0 for dropped lines
+ *   *I_exp_out      = k, the frexp exponent of the largest kept I (device int32)
+ *   *n_kept_out     = number of kept lines (device int64)
+ * A line is kept when nu > 0 (lines with negative centres are discarded,
+ * Sec. 2.4.3), I >= threshold and, if grid != NULL, its cut-off window
+ * [nu - cutoff, nu + cutoff] contains a grid point.
+ * Any output pointer may be NULL except I_exp_out. */
+pxc_status pxc_line_intensities(pxc_workspace* ws, const pxc_states* states,
+                                const pxc_transitions* trans, const pxc_condition* c,
+                                const pxc_grid* grid, double cutoff, double threshold,
+                                double* nu_out, float* I_scaled_out, int32_t* I_exp_out,
+                                int64_t* n_kept_out, cudaStream_t stream);
+
+/* Cross sections, Eq. (xsec): sigma(nu_i) = sum_l I_l f_l(nu_i - nu_l) over the
+ * kept lines with |nu_i - nu_l| <= cutoff, the truncated profile not renormalised.
+ * The window of line l is i_lo = ceil((nu_l - cutoff - nu_min)/dnu),
+ * i_hi = floor((nu_l + cutoff - nu_min)/dnu) in IEEE double.
+ * For each condition j < n_c:
+ *   sigma_out[j * grid.n + i] * 2^sigma_exp_out[j]  (FP32 scaled, exponent int32)
+ * Lines are sorted exactly by (nu, index), binned into grid segments and
+ * accumulated in FP32 with compensated stage sums; nu, the Boltzmann factors
+ * and Q are FP64.  n_c > 1 evaluates the whole (T, P) table in one persistent
+ * launch.  In accumulate mode n_c must be 1. */
+pxc_status pxc_cross_section(pxc_workspace* ws, const pxc_states* states,
+                             const pxc_transitions* trans, const pxc_condition* c, int32_t n_c,
+                             const pxc_grid* grid, const pxc_profile_args* prof, double threshold,
+                             float* sigma_out, int32_t* sigma_exp_out, cudaStream_t stream);
+
+/* Adjoint of a scalar loss L(sigma_s) through pxc_cross_section for ONE
+ * condition (n_c must be 1), given dL_dsigma = dL/dsigma_s on the grid, where
+ * sigma_s is the scaled sigma_out the forward call returns (its exponent is
+ * held constant).  Profiles are recomputed, not stored.  Outputs (device):
+ *   dL_dT[0]         dL/dT (LTE) or dL/dT_rot (two-temperature)   FP64
+ *   dL_dTvib[0]      dL/dT_vib (0 for LTE)                        FP64, nullable
+ *   dL_dP[0]         dL/dP                                        FP64, nullable
+ *   dL_dgamma_ref[t] per transition (0 for dropped lines)         FP32, nullable
+ *   dL_dA[t]         per transition (0 for dropped lines)         FP32, nullable
+ * Kept-line selection (threshold, window) is treated as fixed. */
+pxc_status pxc_cross_section_backward(pxc_workspace* ws, const pxc_states* states,
+                                      const pxc_transitions* trans, const pxc_condition* c, int32_t n_c,
+                                      const pxc_grid* grid, const pxc_profile_args* prof, double threshold,
+                                      const float* dL_dsigma, double* dL_dT, double* dL_dTvib,
+                                      double* dL_dP, float* dL_dgamma_ref, float* dL_dA,
+                                      cudaStream_t stream);
+
+/* Diagnostics of the last pxc_cross_section / backward call on this workspace
+ * (host values; synchronises the stream).  Counts are over the last condition. */
+typedef struct {
+  int64_t n_kept;          /* kept lines */
+  int64_t n_nonzero;       /* kept lines whose FP32 scaled intensity is non-zero */
+  int64_t evals_window;    /* sum over kept lines of their window size (algorithmic count) */
+  int64_t evals_nonzero;   /* the same over kept lines with non-zero scaled intensity */
+  int32_t segment_points;  /* grid points per segment used by the profile kernel */
+  int32_t n_segments;
+  int32_t I_exp;           /* exponent k of the last condition */
+  int32_t reserved;
+} pxc_stats;
+pxc_status pxc_get_stats(pxc_workspace* ws, cudaStream_t stream, pxc_stats* out);
+
+/* The sorted line order and segment binning of the last call (device outputs):
+ * perm_out[j] = transition index of the j-th kept line in (nu bits, index)
+ * order, j < n_kept; seg_first/seg_last [n_segments]: the lines whose windows
+ * meet segment s are perm[seg_first[s] .. seg_last[s]-1].  Nullable. */
+pxc_status pxc_get_binning(pxc_workspace* ws, int64_t* perm_out, int64_t* seg_first,
+                           int64_t* seg_last, cudaStream_t stream);
+
+/* Optional CUDA-event timing of the passes of pxc_cross_section on this
+ * workspace (events recorded on the call's stream around each pass).
+ * pxc_get_timing synchronises `stream` and returns, since the last read,
+ * ms[0] intensity pass, ms[1] compaction + sort + preparation, ms[2] profile
+ * pass, and count[i] the number of timed launches of each (count nullable). */
+pxc_status pxc_set_timing(pxc_workspace* ws, int on);
+pxc_status pxc_get_timing(pxc_workspace* ws, cudaStream_t stream, double* ms, int64_t* count);
+
+/* Stream a HOST-resident line list through the device in chunks of
+ * cap.max_lines transitions (Sec. 2.1: bounded-memory streaming of large
+ * .trans files; Sec. 4.4: one preprocessing pass reused for every output).
+ * Host arrays should be pinned for overlap.  States are device-resident.
+ * Copies of chunk i+1 overlap the kernels of chunk i (two device staging
+ * buffers of dev_chunk_bytes each, caller-owned, from pxc_stream_buffer_bytes).
+ * Result: sigma_out (device) * 2^(*sigma_exp_out) (device int32). */
+size_t pxc_stream_buffer_bytes(int64_t chunk_lines, int32_t A_is_f32, int32_t with_broadening);
+pxc_status pxc_cross_section_streamed(pxc_workspace* ws, const pxc_states* states,
+                                      const int32_t* host_upper, const int32_t* host_lower,
+                                      const void* host_A, int32_t A_is_f32,
+                                      const float* host_gamma_ref, const float* host_n_T,
+                                      int64_t n_lines, const pxc_condition* c,
+                                      const pxc_grid* grid, const pxc_profile_args* prof, double threshold,
+                                      void* dev_chunk_buf0, void* dev_chunk_buf1, size_t dev_chunk_bytes,
+                                      float* sigma_out, int32_t* sigma_exp_out, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PXC_H */

@@ -58,6 +58,7 @@ def _load():
         L.orc_segment_ranges.argtypes = [P, P, i64, i64, i64, P, P]
         L.orc_widths.argtypes = [cint, P, P, P, i64, dbl, dbl, dbl, dbl, dbl, P, P]
         L.orc_cross_section.argtypes = [cint, P, P, P, P, P, P, P, i64, dbl, dbl, i64, P]
+        L.orc_cross_section_window.argtypes = [cint, P, P, P, P, P, P, P, i64, dbl, dbl, i64, i64, P]
         L.orc_cross_section_grad.argtypes = [cint, P, P, P, P, P, cint, P, P, P, P, P, P, P, P, i64,
                                              dbl, dbl, dbl, dbl, P, dbl, dbl, P, P, P, P, P, P]
         _lib = L
@@ -172,6 +173,17 @@ def cross_section(kind, nu, I, alpha, gamma, keep, ilo, ihi, nu_min, dnu, n_grid
     sig = np.empty(n_grid)
     _chk(_load().orc_cross_section(KIND[kind], _p(nu), _p(I), _p(alpha), _p(gamma), _p(keep), _p(ilo), _p(ihi),
                                    nu.size, nu_min, dnu, n_grid, _p(sig)))
+    return sig
+
+
+def cross_section_window(kind, nu, I, alpha, gamma, keep, ilo, ihi, nu_min, dnu, i0, m):
+    """sigma at grid indices i0 .. i0+m-1 only (same grid points as the full grid)."""
+    nu = _c(np.where(keep.astype(bool), nu, 0.0), np.float64)
+    I = _c(I, np.float64); alpha = _c(alpha, np.float64); gamma = _c(gamma, np.float64)
+    keep = _c(keep, np.uint8); ilo = _c(ilo, np.int64); ihi = _c(ihi, np.int64)
+    sig = np.empty(m)
+    _chk(_load().orc_cross_section_window(KIND[kind], _p(nu), _p(I), _p(alpha), _p(gamma), _p(keep), _p(ilo),
+                                          _p(ihi), nu.size, nu_min, dnu, i0, m, _p(sig)))
     return sig
 
 

@@ -22,7 +22,8 @@
  *       i_hi = floor((nu + cut - nu_min)/dnu), plain IEEE double, no FMA,
  *       clamped to the grid; no renormalisation of the truncated profile.
  *   R9  2T stimulated-emission factor 1 - exp(-c2 (nu_vib/T_vib + nu_rot/T_rot)).
- *   R10 threshold: keep I >= S_min.
+ *   R10 threshold: keep |I| >= S_min.  Two-temperature populations can be inverted
+ *       (I < 0, gain); such lines are kept, not silently dropped.
  *   R11 line order: ascending nu bit pattern, ties by transition index.
  *   R12 per-list exponent: k = frexp exponent of max kept I; I_s = (float) ldexp(I, -k).
  *   R15 states with NaN energy are absent: skipped in Q, lines touching them dropped.
@@ -258,7 +259,7 @@ int orc_line_intensities(const double* E, const int32_t* g, const double* E_vib,
       if (x > ORC_EXP_MAX) { status = ORC_ERR_OVERFLOW; break; }
       I = pref * exp(x) * (1.0 - exp(-c2 * nu / T)) / Q;
     }
-    if (!(I >= threshold)) continue;                            /* R10 */
+    if (!(fabs(I) >= threshold)) continue;                      /* R10 */
     I_out[t] = I;
     keep[t] = 1;
     ilo[t] = lo;
@@ -267,11 +268,11 @@ int orc_line_intensities(const double* E, const int32_t* g, const double* E_vib,
   return status;
 }
 
-/* R12: k = exponent of the largest kept intensity (max = m 2^k, 0.5 <= m < 1). */
+/* R12: k = exponent of the largest kept |intensity| (max = m 2^k, 0.5 <= m < 1). */
 int32_t orc_list_exponent(const double* I, const uint8_t* keep, int64_t n) {
   double mx = 0.0;
   for (int64_t t = 0; t < n; ++t)
-    if (keep[t] && I[t] > mx) mx = I[t];
+    if (keep[t] && fabs(I[t]) > mx) mx = fabs(I[t]);
   if (mx == 0.0) return 0;
   int k;
   frexp(mx, &k);
@@ -364,6 +365,26 @@ int orc_cross_section(int kind, const double* nu, const double* I, const double*
         else f = prof_gauss(x, alpha[t]);
         sigma[i] += I[t] * f;
       }
+    }
+  }
+  return ORC_OK;
+}
+
+/* The same sum on the grid points i0 .. i0+m-1 only (sampled checks at full size). */
+int orc_cross_section_window(int kind, const double* nu, const double* I, const double* alpha, const double* gamma,
+                             const uint8_t* keep, const int64_t* ilo, const int64_t* ihi, int64_t n,
+                             double nu_min, double dnu, int64_t i0, int64_t m, double* sigma) {
+  for (int64_t j = 0; j < m; ++j) sigma[j] = 0.0;
+  for (int64_t t = 0; t < n; ++t) {
+    if (!keep[t] || ihi[t] < i0 || ilo[t] > i0 + m - 1) continue;
+    int64_t lo = ilo[t] > i0 ? ilo[t] : i0, hi = ihi[t] < i0 + m - 1 ? ihi[t] : i0 + m - 1;
+    for (int64_t i = lo; i <= hi; ++i) {
+      double x = (nu_min + (double)i * dnu) - nu[t];
+      double f;
+      if (kind == ORC_LORENTZ) f = prof_lorentz(x, gamma[t]);
+      else if (kind == ORC_VOIGT) f = prof_voigt(x, alpha[t], gamma[t]);
+      else f = prof_gauss(x, alpha[t]);
+      sigma[i - i0] += I[t] * f;
     }
   }
   return ORC_OK;

@@ -1,0 +1,123 @@
+// Kernel launchers of the pxc library (host functions, internal).
+#pragma once
+#include "pxc_internal.cuh"
+
+namespace pxc {
+
+// Kernel launches issued by the library since load (all workspaces, all threads).
+void note_launches(int n);
+int64_t launches_total();
+
+// Exact window / position arithmetic parameters (IEEE double, no contraction).
+struct GridP {
+  double nu_min, dnu, cut;
+  int64_t n;
+  double nu_keep_lo, nu_keep_hi;  // nu in [lo, hi] <=> window meets the grid (when exact_bounds)
+  int exact_bounds;               // 0: evaluate the window per line
+};
+
+struct SlotP {                    // one temperature pair
+  double c2_T;                    // c2 / T   (T_rot for two-temperature)
+  double c2_Tv;                   // c2 / T_vib, 0 for LTE
+  double T, T_vib;                // T (T_rot) and T_vib (0 for LTE)
+};
+
+void launch_boltzmann(const pxc_states* st, const SlotP* slots_dev, int nslot, double2* srec, int64_t srec_stride,
+                      double* qpart, double* qres, unsigned* err, cudaStream_t s);
+
+void launch_lines(const pxc_transitions* tr, const int32_t* g, int64_t ns, const double2* srec,
+                  const double* qres, const GridP& gp, int use_grid, double threshold, int with_intensity,
+                  uint64_t* key, double* Iv, double* nu_out, uint32_t* bcount, int64_t nblk,
+                  unsigned long long* maxbits, unsigned* err, cudaStream_t s);
+
+void launch_scan_counts(uint32_t* bcount, int64_t nblk, unsigned long long* total, cudaStream_t s);
+
+void launch_compact(const uint64_t* key, int64_t n, const uint32_t* boff, uint64_t* okey, uint32_t* oidx,
+                    cudaStream_t s);
+
+// Sorts (key, idx) pairs of device count *n_dev (<= n_max) by key, stable.  Result
+// ends in buffer 0 (8 passes).
+void launch_radix_sort(uint64_t* key[2], uint32_t* idx[2], const unsigned long long* n_dev, int64_t n_max,
+                       uint32_t* rcount, cudaStream_t s);
+
+void launch_exponent(const unsigned long long* maxbits, int32_t* kexp, int32_t* sigma_exp_inout,
+                     int accumulate, float* sigma, int64_t n_grid, cudaStream_t s);
+
+void launch_prepare(const uint64_t* skey, const uint32_t* sidx, const unsigned long long* n_dev, int64_t n_max,
+                    const GridP& gp, const float* gamma_ref, const float* n_T, const double* Iv,
+                    const int32_t* kexp, int4* pos, float2* par, float* Is,
+                    const pxc_transitions* gather_tr, int32_t* su, int32_t* sl, double* sA,
+                    int64_t* perm_out, unsigned long long* counters, cudaStream_t s);
+
+void launch_sorted_intensity(const int32_t* su, const int32_t* sl, const double* sA, const unsigned long long* n_dev,
+                             int64_t n_max, const int32_t* g, const double2* srec, const double* qres,
+                             double threshold, double* sI, unsigned long long* maxbits, cudaStream_t s);
+
+void launch_scale(const double* sI, const unsigned long long* n_dev, int64_t n_max, const int32_t* kexp,
+                  float* Is, unsigned long long* counters, cudaStream_t s);
+
+void launch_segments(const int4* pos, const unsigned long long* n_dev, int64_t nseg, int32_t* segr,
+                     cudaStream_t s);
+
+void launch_items(const int32_t* segr, int64_t nseg, int n_c, int item_lines, int32_t* seg_items,
+                  Item* items, unsigned long long* counters, cudaStream_t s);
+
+void launch_reduce_partials(const Item* items, const int32_t* seg_items, int64_t nseg, int n_c,
+                            const float* partial, float* sigma, int64_t n_grid, cudaStream_t s);
+
+void launch_stick_out(const double* Iv, const uint64_t* key, int64_t n, const int32_t* kexp, float* I_scaled,
+                      cudaStream_t s);
+
+// Profile kernels (kernels_profile.cu).
+struct ProfP {
+  const int4* pos;
+  const float2* par;
+  const float* Is;
+  int64_t is_stride;       // floats between intensity slots
+  const CondDev* cond;
+  const Item* items;
+  const unsigned long long* n_items;
+  unsigned long long* queue;
+  float* sigma;            // [n_c][n_grid]
+  float* partial;          // [max_partial][kSeg]
+  int64_t n_grid;
+  double nu_min, dnu;
+  int accumulate;
+  int kind;
+  unsigned* err;
+  long long spin_limit;
+};
+void launch_profile(const ProfP& p, int grid_ctas, cudaStream_t s);
+int profile_occupancy(int kind);
+
+struct AdjP {
+  const int4* pos;
+  const float2* par;
+  const float* Is;
+  const uint32_t* sidx;    // sorted position -> transition index
+  const int32_t* su;       // sorted upper / lower ids
+  const int32_t* sl;
+  const double* sA;
+  const double2* srec;     // {E, b} of the condition's slot
+  const double* E_vib;
+  const float* n_T;        // per transition
+  const double* qres;      // Q, dQ, dQv
+  const float* w;          // dL/dsigma_s [n_grid]
+  const unsigned long long* n_dev;
+  int64_t n_max;
+  int64_t n_grid;
+  double nu_min, dnu, T, T_vib, P, T_ref, c2;
+  CondDev cond;
+  int kind;
+  float* dA;               // [n_trans] by transition index
+  float* dgref;
+  double* lineT;           // [n_max] per-line contributions (sorted order) to the scalars
+  double* lineTv;
+  double* lineP;
+};
+void launch_adjoint(const AdjP& p, cudaStream_t s);
+void launch_adjoint_reduce(const double* lineT, const double* lineTv, const double* lineP,
+                           const unsigned long long* n_dev, int64_t n_max, double* outT, double* outTv,
+                           double* outP, cudaStream_t s);
+
+}  // namespace pxc

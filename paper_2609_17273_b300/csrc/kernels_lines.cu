@@ -1,0 +1,680 @@
+// Line-side kernels: Boltzmann table and partition function, intensity/gather
+// pass, stable compaction, LSD radix sort by (nu bits, index), per-line
+// preparation, segment binning and profile work items.
+#include <atomic>
+#include <cstdio>
+
+#include "kernels.cuh"
+
+namespace pxc {
+
+static std::atomic<int64_t> g_launches{0};
+void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
+
+enum { CNT_QUEUE = 0, CNT_ITEMS = 1, CNT_KEPT = 2, CNT_NONZERO = 3, CNT_EVALS = 4, CNT_EVALS_NZ = 5 };
+
+__device__ __forceinline__ void set_err(unsigned* err, unsigned bits) { atomicOr(err, bits); }
+
+// Window of grid indices of a line (R8): ceil((nu - cut - nu_min)/dnu), floor((nu + cut - nu_min)/dnu),
+// plain IEEE double with explicit rounding intrinsics so no contraction can change a tie.
+__device__ __forceinline__ bool exact_window(double nu, const GridP& gp, int64_t* lo, int64_t* hi) {
+  double a = ceil(__ddiv_rn(__dsub_rn(__dsub_rn(nu, gp.cut), gp.nu_min), gp.dnu));
+  double b = floor(__ddiv_rn(__dsub_rn(__dadd_rn(nu, gp.cut), gp.nu_min), gp.dnu));
+  double top = (double)(gp.n - 1);
+  if (!(b >= 0.0) || a > top || a > b) return false;
+  *lo = a < 0.0 ? 0 : (int64_t)a;
+  *hi = b > top ? gp.n - 1 : (int64_t)b;
+  return true;
+}
+
+__device__ __forceinline__ bool window_meets_grid(double nu, const GridP& gp) {
+  if (gp.exact_bounds) return nu >= gp.nu_keep_lo && nu <= gp.nu_keep_hi;
+  int64_t lo, hi;
+  return exact_window(nu, gp, &lo, &hi);
+}
+
+// ------------------------------------------------------------------ block reductions
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ------------------------------------------------------------------ K-Q: Boltzmann table and Q
+// b_s = exp(-c2 E_s / T) (LTE, Eq. pf) or exp(-c2 E_vib/T_vib - c2 E_rot/T_rot) (Eq. Q nlte 2T);
+// per-block partial sums of g b, g b c2 E_rot / T^2, g b c2 E_vib / T_vib^2 in a fixed order.
+__global__ void __launch_bounds__(kThreadsQ) k_boltzmann(const double* __restrict__ E, const int32_t* __restrict__ g,
+                                                         const double* __restrict__ Ev, int64_t n,
+                                                         const SlotP* __restrict__ slots, int nslot,
+                                                         double2* __restrict__ srec, int64_t stride,
+                                                         double* __restrict__ qpart, unsigned* err) {
+  __shared__ double red[kThreadsQ / 32][3];
+  for (int sl = 0; sl < nslot; ++sl) {
+    const SlotP sp = slots[sl];
+    const bool two_t = sp.c2_Tv > 0.0;
+    double q0 = 0.0, q1 = 0.0, q2 = 0.0;
+    unsigned bad = 0;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+      double e = E[s];
+      double b = 0.0;
+      if (isnan(e)) {
+        b = 0.0;
+      } else if (isinf(e)) {
+        bad |= ERRB_NONFINITE;
+      } else {
+        double x, er = e, ev = 0.0;
+        if (two_t) {
+          ev = Ev[s];
+          er = e - ev;
+          if (!isfinite(ev)) bad |= ERRB_NONFINITE;
+          x = -(ev * sp.c2_Tv) - er * sp.c2_T;
+        } else {
+          x = -e * sp.c2_T;
+        }
+        if (x > kExpMax) {
+          bad |= ERRB_OVERFLOW;
+        } else {
+          b = exp(x);
+          double term = (double)g[s] * b;
+          q0 += term;
+          q1 += term * er * sp.c2_T;   // divided by T in k_qfinal: dQ/dT = sum g b c2 E_rot / T^2
+          q2 += term * ev * sp.c2_Tv;  // divided by T_vib: dQ/dT_vib
+        }
+      }
+      if (srec) srec[(int64_t)sl * stride + s] = make_double2(e, b);
+    }
+    if (bad) set_err(err, bad);
+    // moments: dQ/dT = sum term c2 E_rot / T^2 = (sum term E_rot c2/T) / T
+    q1 = warp_sum(q1); q0 = warp_sum(q0); q2 = warp_sum(q2);
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { red[w][0] = q0; red[w][1] = q1; red[w][2] = q2; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a0 = 0, a1 = 0, a2 = 0;
+      for (int i = 0; i < kThreadsQ / 32; ++i) { a0 += red[i][0]; a1 += red[i][1]; a2 += red[i][2]; }
+      double* o = qpart + ((int64_t)blockIdx.x * nslot + sl) * 3;
+      o[0] = a0; o[1] = a1; o[2] = a2;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_qfinal(const double* __restrict__ qpart, int nblk, int nslot, const SlotP* __restrict__ slots,
+                         double* __restrict__ qres) {
+  __shared__ double red[32][3];
+  int sl = blockIdx.x;
+  double a0 = 0, a1 = 0, a2 = 0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+    const double* o = qpart + ((int64_t)b * nslot + sl) * 3;
+    a0 += o[0]; a1 += o[1]; a2 += o[2];
+  }
+  a0 = warp_sum(a0); a1 = warp_sum(a1); a2 = warp_sum(a2);
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { red[w][0] = a0; red[w][1] = a1; red[w][2] = a2; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { s0 += red[i][0]; s1 += red[i][1]; s2 += red[i][2]; }
+    const SlotP sp = slots[sl];
+    double* r = qres + sl * 4;
+    r[0] = s0;
+    r[1] = s1 / sp.T;                                 // dQ/dT (or dQ/dT_rot)
+    r[2] = sp.c2_Tv > 0.0 ? s2 / sp.T_vib : 0.0;      // dQ/dT_vib
+    r[3] = 1.0 / (8.0 * kPi * kC * s0);
+  }
+}
+
+void launch_boltzmann(const pxc_states* st, const SlotP* slots_dev, int nslot, double2* srec, int64_t srec_stride,
+                      double* qpart, double* qres, unsigned* err, cudaStream_t s) {
+  k_boltzmann<<<kQBlocks, kThreadsQ, 0, s>>>(st->E, st->g, st->E_vib, st->n, slots_dev, nslot, srec, srec_stride,
+                                             qpart, err);
+  k_qfinal<<<nslot, 1024, 0, s>>>(qpart, kQBlocks, nslot, slots_dev, qres);
+  note_launches(2);
+}
+
+// ------------------------------------------------------------------ K-I: intensities
+// nu = E[u] - E[l] (FP64), keep = nu > 0 and window meets the grid and I >= threshold;
+// I = g_u A (b_l - b_u) / (8 pi c nu^2 Q), the Boltzmann factors from the per-state table
+// (b_l - b_u = e^{-c2 E''/T}(1 - e^{-c2 nu/T}) for LTE, and the Treanor form of Eq.
+// (nlte ab 2T) for two temperatures since b_u/b_l = e^{-c2(nu_vib/T_vib + nu_rot/T_rot)}).
+__global__ void __launch_bounds__(kThreadsI) k_lines(const int32_t* __restrict__ up, const int32_t* __restrict__ lo,
+                                                     const void* __restrict__ Av, int A32, int64_t n,
+                                                     const double2* __restrict__ srec, const int32_t* __restrict__ g,
+                                                     int64_t ns, const double* __restrict__ qres, GridP gp,
+                                                     int use_grid, double threshold, int with_I,
+                                                     uint64_t* __restrict__ key, double* __restrict__ Iv,
+                                                     double* __restrict__ nu_out, uint32_t* __restrict__ bcount,
+                                                     unsigned long long* __restrict__ maxbits, unsigned* err) {
+  __shared__ uint32_t wk[kThreadsI / 32];
+  __shared__ unsigned long long wm[kThreadsI / 32];
+  const double invQ = with_I ? qres[3] : 0.0;
+  const int64_t base = (int64_t)blockIdx.x * kLinesPerBlockI;
+  uint32_t kept = 0;
+  unsigned long long mx = 0;
+  unsigned bad = 0;
+#pragma unroll 2
+  for (int k = 0; k < kLinesPerBlockI / kThreadsI; ++k) {
+    int64_t t = base + k * kThreadsI + threadIdx.x;
+    if (t >= n) break;
+    int64_t u = up[t], l = lo[t];
+    double A = A32 ? (double)((const float*)Av)[t] : ((const double*)Av)[t];
+    uint64_t kk = kSentinelKey;
+    double I = 0.0;
+    double nu = __longlong_as_double(0x7ff8000000000000ll);
+    if (u < 0 || u >= ns || l < 0 || l >= ns) {
+      bad |= ERRB_ID;
+    } else {
+      if (!isfinite(A)) bad |= ERRB_NONFINITE;
+      double2 ru = srec[u], rl = srec[l];
+      nu = __dsub_rn(ru.x, rl.x);
+      bool keep = nu > 0.0;
+      if (keep && use_grid) keep = window_meets_grid(nu, gp);
+      if (keep && with_I) {
+        // |I| >= threshold tested as |num| >= threshold * nu^2 (no division for dropped lines)
+        const double num = (double)g[u] * A * invQ * (rl.y - ru.y);
+        const double den = nu * nu;
+        keep = fabs(num) >= threshold * den;
+        if (keep) I = num / den;
+      }
+      if (keep) {
+        kk = (uint64_t)__double_as_longlong(nu);
+        ++kept;
+        unsigned long long ib = (unsigned long long)__double_as_longlong(fabs(I));
+        mx = ib > mx ? ib : mx;
+      } else {
+        I = 0.0;
+      }
+    }
+    key[t] = kk;
+    if (with_I) Iv[t] = I;
+    if (nu_out) nu_out[t] = nu;
+  }
+  if (bad) set_err(err, bad);
+  kept = warp_sum(kept);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long v = __shfl_down_sync(0xffffffffu, mx, o);
+    mx = v > mx ? v : mx;
+  }
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { wk[w] = kept; wm[w] = mx; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t s = 0;
+    unsigned long long m = 0;
+    for (int i = 0; i < kThreadsI / 32; ++i) { s += wk[i]; m = wm[i] > m ? wm[i] : m; }
+    bcount[blockIdx.x] = s;
+    if (with_I && m) atomicMax(maxbits, m);
+  }
+}
+
+void launch_lines(const pxc_transitions* tr, const int32_t* g, int64_t ns, const double2* srec,
+                  const double* qres, const GridP& gp, int use_grid, double threshold, int with_intensity,
+                  uint64_t* key, double* Iv, double* nu_out, uint32_t* bcount, int64_t nblk,
+                  unsigned long long* maxbits, unsigned* err, cudaStream_t s) {
+  if (nblk == 0) return;
+  k_lines<<<(unsigned)nblk, kThreadsI, 0, s>>>(tr->upper, tr->lower, tr->A, tr->A_is_f32, tr->n, srec, g, ns, qres,
+                                               gp, use_grid, threshold, with_intensity, key, Iv, nu_out, bcount,
+                                               maxbits, err);
+  note_launches(1);
+}
+
+// ------------------------------------------------------------------ exclusive scan of block counts (one CTA)
+__global__ void k_scan_counts(uint32_t* __restrict__ c, int64_t n, unsigned long long* total) {
+  __shared__ unsigned long long part[1024];
+  int64_t per = (n + blockDim.x - 1) / blockDim.x;
+  int64_t a = threadIdx.x * per, b = a + per < n ? a + per : n;
+  unsigned long long s = 0;
+  for (int64_t i = a; i < b; ++i) s += c[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long run = 0;
+    for (int i = 0; i < (int)blockDim.x; ++i) { unsigned long long v = part[i]; part[i] = run; run += v; }
+    *total = run;
+  }
+  __syncthreads();
+  unsigned long long run = part[threadIdx.x];
+  for (int64_t i = a; i < b; ++i) { uint32_t v = c[i]; c[i] = (uint32_t)run; run += v; }
+}
+
+void launch_scan_counts(uint32_t* bcount, int64_t nblk, unsigned long long* total, cudaStream_t s) {
+  k_scan_counts<<<1, 1024, 0, s>>>(bcount, nblk, total);
+  note_launches(1);
+}
+
+// ------------------------------------------------------------------ stable compaction of kept keys
+__global__ void __launch_bounds__(kThreadsI) k_compact(const uint64_t* __restrict__ key, int64_t n,
+                                                       const uint32_t* __restrict__ boff, uint64_t* __restrict__ okey,
+                                                       uint32_t* __restrict__ oidx) {
+  __shared__ uint32_t wsum[kThreadsI / 32];
+  const int64_t base = (int64_t)blockIdx.x * kLinesPerBlockI;
+  uint32_t run = boff[blockIdx.x];
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = 0; k < kLinesPerBlockI / kThreadsI; ++k) {
+    int64_t t = base + k * kThreadsI + threadIdx.x;
+    uint64_t kk = t < n ? key[t] : kSentinelKey;
+    bool keep = kk != kSentinelKey;
+    unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) wsum[w] = __popc(m);
+    __syncthreads();
+    uint32_t before = 0, tot = 0;
+    for (int i = 0; i < kThreadsI / 32; ++i) { before += i < w ? wsum[i] : 0; tot += wsum[i]; }
+    if (keep) {
+      uint32_t p = run + before + __popc(m & ((1u << lane) - 1u));
+      okey[p] = kk;
+      oidx[p] = (uint32_t)(t - 0);
+    }
+    run += tot;
+    __syncthreads();
+  }
+}
+
+void launch_compact(const uint64_t* key, int64_t n, const uint32_t* boff, uint64_t* okey, uint32_t* oidx,
+                    cudaStream_t s) {
+  int64_t nblk = (n + kLinesPerBlockI - 1) / kLinesPerBlockI;
+  if (nblk == 0) return;
+  k_compact<<<(unsigned)nblk, kThreadsI, 0, s>>>(key, n, boff, okey, oidx);
+  note_launches(1);
+}
+
+// ------------------------------------------------------------------ LSD radix sort, 8 passes of 8 bits
+// Pass: per-tile digit histogram -> per-digit exclusive scan over tiles -> stable scatter.
+__global__ void __launch_bounds__(kSortThreads) k_hist(const uint64_t* __restrict__ key,
+                                                       const unsigned long long* __restrict__ n_dev, int64_t nblk,
+                                                       int shift, uint32_t* __restrict__ cnt) {
+  __shared__ uint32_t h[256];
+  const int64_t n = (int64_t)*n_dev;
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  if (base < n) {
+    for (int i = 0; i < kSortItems; ++i) {
+      int64_t j = base + i * kSortThreads + threadIdx.x;
+      if (j < n) atomicAdd(&h[(unsigned)(key[j] >> shift) & 255u], 1u);
+    }
+  }
+  __syncthreads();
+  cnt[(int64_t)threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
+}
+
+// One CTA per digit: exclusive scan of that digit's row over the active tiles; row total at the end.
+__global__ void k_rowscan(uint32_t* __restrict__ cnt, const unsigned long long* __restrict__ n_dev, int64_t nblk,
+                          uint32_t* __restrict__ rowtot) {
+  __shared__ uint32_t part[1024];
+  const int64_t n = (int64_t)*n_dev;
+  const int64_t act = (n + kSortTile - 1) / kSortTile;
+  uint32_t* row = cnt + (int64_t)blockIdx.x * nblk;
+  int64_t per = (act + blockDim.x - 1) / blockDim.x;
+  int64_t a = threadIdx.x * per, b = a + per < act ? a + per : act;
+  uint32_t s = 0;
+  for (int64_t i = a; i < b; ++i) s += row[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  // Hillis-Steele inclusive scan over the 1024 partials
+  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+    uint32_t v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  uint32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
+  for (int64_t i = a; i < b; ++i) { uint32_t v = row[i]; row[i] = run; run += v; }
+  if (threadIdx.x == blockDim.x - 1) rowtot[blockIdx.x] = part[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_scatter(const uint64_t* __restrict__ key,
+                                                          const uint32_t* __restrict__ idx,
+                                                          const unsigned long long* __restrict__ n_dev, int64_t nblk,
+                                                          int shift, const uint32_t* __restrict__ cnt,
+                                                          const uint32_t* __restrict__ rowtot,
+                                                          uint64_t* __restrict__ okey, uint32_t* __restrict__ oidx) {
+  __shared__ uint32_t wc[kSortThreads / 32][256];
+  __shared__ uint32_t dbase[256];
+  const int64_t n = (int64_t)*n_dev;
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  if (base >= n) return;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int d = threadIdx.x; d < 256 * (kSortThreads / 32); d += kSortThreads) (&wc[0][0])[d] = 0;
+  // digit bases: exclusive scan of the row totals (thread d computes its own base serially over 256 -> cheap)
+  {
+    uint32_t s = 0;
+    for (int d = 0; d < (int)threadIdx.x; ++d) s += rowtot[d];
+    dbase[threadIdx.x] = s + cnt[(int64_t)threadIdx.x * nblk + blockIdx.x];
+  }
+  __syncthreads();
+  uint64_t kv[kSortItems];
+  uint32_t iv[kSortItems];
+  uint32_t rk[kSortItems];
+  const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i) {
+    int64_t j = base + (int64_t)w * (32 * kSortItems) + i * 32 + lane;
+    bool v = j < n;
+    kv[i] = v ? key[j] : 0;
+    iv[i] = v ? idx[j] : 0;
+    unsigned d = v ? ((unsigned)(kv[i] >> shift) & 255u) : 256u;
+    unsigned peers = __match_any_sync(0xffffffffu, d);
+    unsigned b = d < 256u ? wc[w][d] : 0u;
+    __syncwarp();
+    if (d < 256u && lane == __ffs(peers) - 1) wc[w][d] = b + __popc(peers);
+    __syncwarp();
+    rk[i] = v ? (b + __popc(peers & lt)) | (d << 20) : 0xffffffffu;
+  }
+  __syncthreads();
+  // exclusive scan over warps for each digit
+  {
+    uint32_t run = 0;
+    for (int ww = 0; ww < kSortThreads / 32; ++ww) {
+      uint32_t t = wc[ww][threadIdx.x];
+      wc[ww][threadIdx.x] = run;
+      run += t;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i) {
+    if (rk[i] == 0xffffffffu) continue;
+    unsigned d = rk[i] >> 20, r = rk[i] & 0xfffffu;
+    uint32_t p = dbase[d] + wc[w][d] + r;
+    okey[p] = kv[i];
+    oidx[p] = iv[i];
+  }
+}
+
+void launch_radix_sort(uint64_t* key[2], uint32_t* idx[2], const unsigned long long* n_dev, int64_t n_max,
+                       uint32_t* rcount, cudaStream_t s) {
+  int64_t nblk = (n_max + kSortTile - 1) / kSortTile;
+  if (nblk == 0) return;
+  uint32_t* rowtot = rcount + 256 * nblk;
+  for (int pass = 0; pass < 8; ++pass) {
+    int src = pass & 1, dst = src ^ 1;
+    int shift = pass * 8;
+    k_hist<<<(unsigned)nblk, kSortThreads, 0, s>>>(key[src], n_dev, nblk, shift, rcount);
+    k_rowscan<<<256, 1024, 0, s>>>(rcount, n_dev, nblk, rowtot);
+    k_scatter<<<(unsigned)nblk, kSortThreads, 0, s>>>(key[src], idx[src], n_dev, nblk, shift, rcount, rowtot,
+                                                      key[dst], idx[dst]);
+  }
+  note_launches(24);
+}
+
+// ------------------------------------------------------------------ list exponent
+// k = frexp exponent of the largest kept |intensity| (R12); in accumulate mode the
+// running sum's exponent is raised to max(k_run, k) and the sum rescaled exactly.
+__global__ void k_exponent(const unsigned long long* maxbits, int32_t* kexp, int32_t* sig_exp, int accumulate) {
+  double mx = __longlong_as_double((long long)*maxbits);
+  int k = 0;
+  if (mx > 0.0) frexp(mx, &k);
+  if (accumulate && sig_exp) {
+    int old = *sig_exp;
+    if (old != PXC_EXP_EMPTY && (old > k || !(mx > 0.0))) k = old;
+    kexp[1] = old;  // previous exponent, for the rescale kernel
+  }
+  kexp[0] = k;
+  if (sig_exp) *sig_exp = k;
+}
+
+__global__ void k_rescale(float* sigma, int64_t n, const int32_t* kexp) {
+  int old = kexp[1], k = kexp[0];
+  if (old == PXC_EXP_EMPTY || old == k) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    sigma[i] = ldexpf(sigma[i], old - k);
+}
+
+void launch_exponent(const unsigned long long* maxbits, int32_t* kexp, int32_t* sigma_exp_inout, int accumulate,
+                     float* sigma, int64_t n_grid, cudaStream_t s) {
+  k_exponent<<<1, 1, 0, s>>>(maxbits, kexp, sigma_exp_inout, accumulate);
+  note_launches(1);
+  if (accumulate && sigma) { k_rescale<<<592, 256, 0, s>>>(sigma, n_grid, kexp); note_launches(1); }
+}
+
+// ------------------------------------------------------------------ prepare sorted lines
+// pos = {ic, f, ilo, ihi} with (nu - nu_min)/dnu = ic + f, par = {gamma_ref, n_T}, Is = ldexp(I, -k).
+__global__ void __launch_bounds__(256) k_prepare(const uint64_t* __restrict__ skey, const uint32_t* __restrict__ sidx,
+                                                 const unsigned long long* __restrict__ n_dev, GridP gp,
+                                                 const float* __restrict__ gref, const float* __restrict__ nT,
+                                                 const double* __restrict__ Iv, const int32_t* __restrict__ kexp,
+                                                 int4* __restrict__ pos, float2* __restrict__ par,
+                                                 float* __restrict__ Is, const int32_t* __restrict__ up,
+                                                 const int32_t* __restrict__ lo, const void* __restrict__ Av, int A32,
+                                                 int32_t* __restrict__ su, int32_t* __restrict__ sl,
+                                                 double* __restrict__ sA, int64_t* __restrict__ perm,
+                                                 unsigned long long* __restrict__ counters) {
+  const int64_t n = (int64_t)*n_dev;
+  const int k = Iv ? kexp[0] : 0;
+  unsigned long long ev = 0, evnz = 0, nz = 0;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    double nu = __longlong_as_double((long long)skey[j]);
+    uint32_t t = sidx[j];
+    int64_t a = 0, b = -1;
+    exact_window(nu, gp, &a, &b);
+    double c = __ddiv_rn(__dsub_rn(nu, gp.nu_min), gp.dnu);
+    double fc = floor(c);
+    float f = (float)__dsub_rn(c, fc);
+    pos[j] = make_int4((int)fc, __float_as_int(f), (int)a, (int)b);
+    par[j] = gref ? make_float2(gref[t], nT[t]) : make_float2(0.f, 0.f);
+    unsigned long long wsz = (unsigned long long)(b - a + 1);
+    ev += wsz;
+    if (Iv) {
+      float is = (float)ldexp(Iv[t], -k);
+      Is[j] = is;
+      if (is != 0.f) { evnz += wsz; ++nz; }
+    }
+    if (su) {
+      su[j] = up[t];
+      sl[j] = lo[t];
+      sA[j] = A32 ? (double)((const float*)Av)[t] : ((const double*)Av)[t];
+    }
+    if (perm) perm[j] = (int64_t)t;
+  }
+  ev = warp_sum(ev); evnz = warp_sum(evnz); nz = warp_sum(nz);
+  if ((threadIdx.x & 31) == 0) {
+    if (ev) atomicAdd(&counters[CNT_EVALS], ev);
+    if (evnz) atomicAdd(&counters[CNT_EVALS_NZ], evnz);
+    if (nz) atomicAdd(&counters[CNT_NONZERO], nz);
+  }
+}
+
+void launch_prepare(const uint64_t* skey, const uint32_t* sidx, const unsigned long long* n_dev, int64_t n_max,
+                    const GridP& gp, const float* gamma_ref, const float* n_T, const double* Iv,
+                    const int32_t* kexp, int4* pos, float2* par, float* Is,
+                    const pxc_transitions* gather_tr, int32_t* su, int32_t* sl, double* sA,
+                    int64_t* perm_out, unsigned long long* counters, cudaStream_t s) {
+  if (n_max == 0) return;
+  int64_t blocks = (n_max + 255) / 256;
+  if (blocks > 148 * 16) blocks = 148 * 16;
+  k_prepare<<<(unsigned)blocks, 256, 0, s>>>(skey, sidx, n_dev, gp, gamma_ref, n_T, Iv, kexp, pos, par, Is,
+                                            gather_tr ? gather_tr->upper : nullptr,
+                                            gather_tr ? gather_tr->lower : nullptr,
+                                            gather_tr ? gather_tr->A : nullptr, gather_tr ? gather_tr->A_is_f32 : 0,
+                                            su, sl, sA, perm_out, counters);
+  note_launches(1);
+}
+
+// ------------------------------------------------------------------ batched intensities in sorted order
+__global__ void __launch_bounds__(256) k_sorted_intensity(const int32_t* __restrict__ su, const int32_t* __restrict__ sl,
+                                                          const double* __restrict__ sA,
+                                                          const unsigned long long* __restrict__ n_dev,
+                                                          const int32_t* __restrict__ g,
+                                                          const double2* __restrict__ srec,
+                                                          const double* __restrict__ qres, double threshold,
+                                                          double* __restrict__ sI,
+                                                          unsigned long long* __restrict__ maxbits) {
+  const int64_t n = (int64_t)*n_dev;
+  const double invQ = qres[3];
+  unsigned long long mx = 0;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    int32_t u = su[j], l = sl[j];
+    double2 ru = srec[u], rl = srec[l];
+    double nu = __dsub_rn(ru.x, rl.x);
+    const double num = (double)g[u] * sA[j] * invQ * (rl.y - ru.y);
+    const double den = nu * nu;
+    double I = fabs(num) >= threshold * den ? num / den : 0.0;
+    sI[j] = I;
+    unsigned long long ib = (unsigned long long)__double_as_longlong(fabs(I));
+    mx = ib > mx ? ib : mx;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long v = __shfl_down_sync(0xffffffffu, mx, o);
+    mx = v > mx ? v : mx;
+  }
+  if ((threadIdx.x & 31) == 0 && mx) atomicMax(maxbits, mx);
+}
+
+void launch_sorted_intensity(const int32_t* su, const int32_t* sl, const double* sA, const unsigned long long* n_dev,
+                             int64_t n_max, const int32_t* g, const double2* srec, const double* qres,
+                             double threshold, double* sI, unsigned long long* maxbits, cudaStream_t s) {
+  if (n_max == 0) return;
+  int64_t blocks = (n_max + 255) / 256;
+  if (blocks > 148 * 16) blocks = 148 * 16;
+  k_sorted_intensity<<<(unsigned)blocks, 256, 0, s>>>(su, sl, sA, n_dev, g, srec, qres, threshold, sI, maxbits);
+  note_launches(1);
+}
+
+__global__ void k_scale(const double* __restrict__ sI, const unsigned long long* __restrict__ n_dev,
+                        const int32_t* __restrict__ kexp, float* __restrict__ Is) {
+  const int64_t n = (int64_t)*n_dev;
+  const int k = kexp[0];
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    Is[j] = (float)ldexp(sI[j], -k);
+}
+
+void launch_scale(const double* sI, const unsigned long long* n_dev, int64_t n_max, const int32_t* kexp,
+                  float* Is, unsigned long long* counters, cudaStream_t s) {
+  (void)counters;
+  if (n_max == 0) return;
+  int64_t blocks = (n_max + 255) / 256;
+  if (blocks > 148 * 16) blocks = 148 * 16;
+  k_scale<<<(unsigned)blocks, 256, 0, s>>>(sI, n_dev, kexp, Is);
+  note_launches(1);
+}
+
+// ------------------------------------------------------------------ segment binning
+// Windows are monotone in nu, so the lines meeting segment s = [s S, (s+1) S) are the
+// contiguous sorted range [first, last): first = #lines with ihi < s S, last = #lines with ilo <= (s+1) S - 1.
+__global__ void k_segments(const int4* __restrict__ pos, const unsigned long long* __restrict__ n_dev, int64_t nseg,
+                           int32_t* __restrict__ segr) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nseg) return;
+  const int64_t n = (int64_t)*n_dev;
+  const int64_t a = s * kSeg, b = (s + 1) * kSeg - 1;
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    int64_t m = (lo + hi) >> 1;
+    if ((int64_t)pos[m].w < a) lo = m + 1; else hi = m;
+  }
+  int64_t first = lo;
+  lo = first; hi = n;
+  while (lo < hi) {
+    int64_t m = (lo + hi) >> 1;
+    if ((int64_t)pos[m].z <= b) lo = m + 1; else hi = m;
+  }
+  segr[s] = (int32_t)first;
+  segr[nseg + s] = (int32_t)lo;
+}
+
+void launch_segments(const int4* pos, const unsigned long long* n_dev, int64_t nseg, int32_t* segr, cudaStream_t s) {
+  k_segments<<<(unsigned)((nseg + 255) / 256), 256, 0, s>>>(pos, n_dev, nseg, segr);
+  note_launches(1);
+}
+
+// Work items: each (condition, segment) group is split into ceil(lines / item_lines) items (at least one).
+__global__ void k_items(const int32_t* __restrict__ segr, int64_t nseg, int n_c, int item_lines,
+                        int32_t* __restrict__ seg_items, Item* __restrict__ items,
+                        unsigned long long* __restrict__ counters) {
+  __shared__ unsigned long long part[1024];
+  const int64_t ng = nseg * n_c;
+  int64_t per = (ng + blockDim.x - 1) / blockDim.x;
+  int64_t a = threadIdx.x * per, b = a + per < ng ? a + per : ng;
+  auto count = [&](int64_t gi) -> int64_t {
+    int64_t s = gi % nseg;
+    int64_t nl = (int64_t)segr[nseg + s] - segr[s];
+    int64_t c = (nl + item_lines - 1) / item_lines;
+    return c < 1 ? 1 : c;
+  };
+  unsigned long long sum = 0;
+  for (int64_t i = a; i < b; ++i) sum += count(i);
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long run = 0;
+    for (int i = 0; i < (int)blockDim.x; ++i) { unsigned long long v = part[i]; part[i] = run; run += v; }
+    seg_items[ng] = (int32_t)run;
+    counters[CNT_ITEMS] = run;
+    counters[CNT_QUEUE] = 0;
+  }
+  __syncthreads();
+  unsigned long long run = part[threadIdx.x];
+  for (int64_t gi = a; gi < b; ++gi) {
+    int64_t c = count(gi);
+    seg_items[gi] = (int32_t)run;
+    int64_t s = gi % nseg;
+    int32_t f = segr[s], e = segr[nseg + s];
+    for (int64_t k = 0; k < c; ++k) {
+      Item it;
+      it.cond = (int32_t)(gi / nseg);
+      it.seg = (int32_t)s;
+      it.begin = (int32_t)(f + k * item_lines);
+      int64_t en = (int64_t)f + (k + 1) * item_lines;
+      it.end = (int32_t)(en < e ? en : e);
+      if (it.begin > e) it.begin = e;
+      int64_t idx = (int64_t)run + k;
+      it.slot = k == 0 ? -1 : (int32_t)(idx - gi - 1);
+      it.first_of_seg = (int32_t)run;
+      it.n_of_seg = (int32_t)c;
+      it.pad = 0;
+      items[idx] = it;
+    }
+    run += c;
+  }
+}
+
+void launch_items(const int32_t* segr, int64_t nseg, int n_c, int item_lines, int32_t* seg_items, Item* items,
+                  unsigned long long* counters, cudaStream_t s) {
+  k_items<<<1, 1024, 0, s>>>(segr, nseg, n_c, item_lines, seg_items, items, counters);
+  note_launches(1);
+}
+
+// Adds the partial rows of split segments to sigma, in item order (deterministic).
+__global__ void k_reduce_partials(const Item* __restrict__ items, const int32_t* __restrict__ seg_items, int64_t nseg,
+                                  const float* __restrict__ partial, float* __restrict__ sigma, int64_t n_grid) {
+  int64_t gi = blockIdx.x;
+  int32_t f = seg_items[gi], e = seg_items[gi + 1];
+  if (e - f <= 1) return;
+  int64_t s = gi % nseg, c = gi / nseg;
+  for (int p = threadIdx.x; p < kSeg; p += blockDim.x) {
+    int64_t i = s * kSeg + p;
+    if (i >= n_grid) break;
+    float v = sigma[c * n_grid + i];
+    for (int32_t it = f + 1; it < e; ++it) v += partial[(int64_t)items[it].slot * kSeg + p];
+    sigma[c * n_grid + i] = v;
+  }
+}
+
+void launch_reduce_partials(const Item* items, const int32_t* seg_items, int64_t nseg, int n_c,
+                            const float* partial, float* sigma, int64_t n_grid, cudaStream_t s) {
+  k_reduce_partials<<<(unsigned)(nseg * n_c), 256, 0, s>>>(items, seg_items, nseg, partial, sigma, n_grid);
+  note_launches(1);
+}
+
+// ------------------------------------------------------------------ stick-spectrum output
+__global__ void k_stick_out(const double* __restrict__ Iv, const uint64_t* __restrict__ key, int64_t n,
+                            const int32_t* __restrict__ kexp, float* __restrict__ out) {
+  const int k = kexp[0];
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    out[t] = key[t] == kSentinelKey ? 0.f : (float)ldexp(Iv[t], -k);
+}
+
+void launch_stick_out(const double* Iv, const uint64_t* key, int64_t n, const int32_t* kexp, float* I_scaled,
+                      cudaStream_t s) {
+  if (n == 0) return;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 148 * 16) blocks = 148 * 16;
+  k_stick_out<<<(unsigned)blocks, 256, 0, s>>>(Iv, key, n, kexp, I_scaled);
+  note_launches(1);
+}
+
+}  // namespace pxc

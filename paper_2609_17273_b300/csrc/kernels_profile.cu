@@ -1,0 +1,587 @@
+// Profile accumulation (Eq. xsec over the kept lines) and its adjoint.
+//
+// Forward: persistent CTAs take work items (condition, grid segment of kSeg
+// points, a contiguous range of the nu-sorted lines whose windows meet the
+// segment).  Thread t owns the points t + 256 q, q < kPts, in registers.  The
+// line records (position, broadening parameters, scaled intensity) are staged
+// into shared memory by 1-D bulk TMA copies (cp.async.bulk) completing on an
+// mbarrier, kStages buffers deep; every wait is bounded.  Per stage, each thread
+// turns one record into the line's constants, then every thread evaluates all
+// staged lines at its points (FP32, no atomics).  Stage sums are folded into a
+// compensated (two-sum) accumulator.
+//
+// Voigt uses Humlicek's W4 rational approximation of the Faddeeva function
+// (J. Humlicek, JQSRT 27 (1982) 437), the method the paper recommends for GPU
+// Voigt evaluation (Sec. 4.1): region I (|x|+y >= 15) is the one-level
+// Laplace continued fraction t/sqrt(pi)/(1/2 + t^2), t = y - ix, whose real part
+// needs one reciprocal; lines whose whole segment lies in region I and inside
+// the cut-off window take a branch-free path.
+#include <cstdio>
+
+#include "kernels.cuh"
+
+namespace pxc {
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// Bounded wait: true if the phase completed, false after `limit` clock cycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, long long limit) {
+  if (mbar_try_wait(bar, parity)) return true;
+  long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > limit) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ float frcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float fex2(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// ------------------------------------------------------------------ Humlicek W4 (FP32)
+struct cplx {
+  float r, i;
+};
+__device__ __forceinline__ cplx cmul(cplx a, cplx b) { return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r}; }
+__device__ __forceinline__ cplx cadd(cplx a, float b) { return {a.r + b, a.i}; }
+__device__ __forceinline__ cplx csub_from(float a, cplx b) { return {a - b.r, -b.i}; }
+__device__ __forceinline__ cplx cdiv(cplx a, cplx b) {
+  float d = frcp(b.r * b.r + b.i * b.i);
+  return {(a.r * b.r + a.i * b.i) * d, (a.i * b.r - a.r * b.i) * d};
+}
+
+// Complex W4 value w(z) and dw/dz, z = x + iy (y >= 0).  Regions as published:
+// I: s >= 15, II: 5.5 <= s < 15, III: s < 5.5 and y >= 0.195|x| - 0.176, IV otherwise.
+__device__ __noinline__ void w4_full(float x, float y, cplx* w, cplx* dw) {
+  const float ax = fabsf(x), s = ax + y;
+  const cplx t = {y, -x};
+  const cplx u = cmul(t, t);
+  cplx dwdt;
+  if (s >= 15.f) {
+    // w = t N / D, N = 1/sqrt(pi), D = 1/2 + u;  dw/dt = N (1/2 - u) / D^2
+    cplx D = cadd(u, 0.5f);
+    *w = cdiv({t.r * kInvSqrtPi, t.i * kInvSqrtPi}, D);
+    cplx D2 = cmul(D, D);
+    dwdt = cdiv({kInvSqrtPi * (0.5f - u.r), -kInvSqrtPi * u.i}, D2);
+  } else if (s >= 5.5f) {
+    // w = t N(u) / D(u), N = a + b u, D = c + 3u + u^2; dw/dt = [N D + 2u (N' D - N D')] / D^2
+    const float a = 1.410474f, b = 0.5641896f;
+    cplx N = {a + b * u.r, b * u.i};
+    cplx D = cadd(cmul(u, cadd(u, 3.f)), 0.75f);
+    *w = cdiv(cmul(t, N), D);
+    cplx Dp = {3.f + 2.f * u.r, 2.f * u.i};
+    cplx inner = {b * D.r - (N.r * Dp.r - N.i * Dp.i), b * D.i - (N.r * Dp.i + N.i * Dp.r)};
+    cplx two_u = {2.f * u.r, 2.f * u.i};
+    cplx num = cmul(N, D);
+    cplx add = cmul(two_u, inner);
+    dwdt = cdiv({num.r + add.r, num.i + add.i}, cmul(D, D));
+  } else if (y >= 0.195f * ax - 0.176f) {
+    // w = P(t) / Q(t)
+    cplx P = cadd(cmul(t, cadd(cmul(t, cadd(cmul(t, cadd(cmul(t, {0.5642236f, 0.f}), 3.778987f)), 11.96482f)), 20.20933f)),
+                  16.4955f);
+    cplx Q = cadd(cmul(t, cadd(cmul(t, cadd(cmul(t, cadd(cmul(t, cadd(t, 6.699398f)), 21.69274f)), 39.27121f)),
+                               38.82363f)),
+                  16.4955f);
+    *w = cdiv(P, Q);
+    // derivatives of the polynomials
+    cplx Pp = cadd(cmul(t, cadd(cmul(t, cadd(cmul(t, {4.f * 0.5642236f, 0.f}), 3.f * 3.778987f)), 2.f * 11.96482f)),
+                   20.20933f);
+    cplx Qp = cadd(cmul(t, cadd(cmul(t, cadd(cmul(t, cadd({5.f * t.r, 5.f * t.i}, 4.f * 6.699398f)), 3.f * 21.69274f)),
+                               2.f * 39.27121f)),
+                   38.82363f);
+    cplx a1 = cmul(Pp, Q), a2 = cmul(P, Qp);
+    dwdt = cdiv({a1.r - a2.r, a1.i - a2.i}, cmul(Q, Q));
+  } else {
+    // w = exp(u) - t P(u) / Q(u)
+    cplx P = csub_from(36183.31f, cmul(u, csub_from(3321.9905f, cmul(u, csub_from(1540.787f, cmul(u, csub_from(219.0313f,
+                 cmul(u, csub_from(35.76683f, cmul(u, csub_from(1.320522f, {0.56419f * u.r, 0.56419f * u.i})))))))))));
+    cplx Q = csub_from(32066.6f, cmul(u, csub_from(24322.84f, cmul(u, csub_from(9022.228f, cmul(u, csub_from(2186.181f,
+                 cmul(u, csub_from(364.2191f, cmul(u, csub_from(61.57037f, cmul(u, csub_from(1.841439f, u)))))))))))));
+    float eu = expf(u.r);
+    float sn, cs;
+    sincosf(u.i, &sn, &cs);
+    cplx e = {eu * cs, eu * sn};
+    cplx R = cdiv(P, Q);
+    cplx tR = cmul(t, R);
+    *w = {e.r - tR.r, e.i - tR.i};
+    // P'(u), Q'(u)
+    cplx Pp = {-3321.9905f, 0.f};
+    {
+      // P(u) = 36183.31 - 3321.9905 u + 1540.787 u^2 - 219.0313 u^3 + 35.76683 u^4 - 1.320522 u^5 + 0.56419 u^6
+      const float c[7] = {36183.31f, -3321.9905f, 1540.787f, -219.0313f, 35.76683f, -1.320522f, 0.56419f};
+      cplx acc = {6.f * c[6], 0.f};
+      for (int k = 5; k >= 1; --k) acc = cadd(cmul(acc, u), (float)k * c[k]);
+      Pp = acc;
+    }
+    cplx Qp;
+    {
+      // Q(u) = 32066.6 - 24322.84 u + 9022.228 u^2 - 2186.181 u^3 + 364.2191 u^4 - 61.57037 u^5 + 1.841439 u^6 - u^7
+      const float c[8] = {32066.6f, -24322.84f, 9022.228f, -2186.181f, 364.2191f, -61.57037f, 1.841439f, -1.f};
+      cplx acc = {7.f * c[7], 0.f};
+      for (int k = 6; k >= 1; --k) acc = cadd(cmul(acc, u), (float)k * c[k]);
+      Qp = acc;
+    }
+    // d/dt [t R(u)] = R + 2u R'(u), R' = (P'Q - PQ')/Q^2
+    cplx a1 = cmul(Pp, Q), a2 = cmul(P, Qp);
+    cplx Rp = cdiv({a1.r - a2.r, a1.i - a2.i}, cmul(Q, Q));
+    cplx two_u = {2.f * u.r, 2.f * u.i};
+    cplx dtR = cmul(two_u, Rp);
+    cplx two_t_e = cmul({2.f * t.r, 2.f * t.i}, e);
+    dwdt = {two_t_e.r - R.r - dtR.r, two_t_e.i - R.i - dtR.i};
+  }
+  // t = -i z  =>  dw/dz = -i dw/dt
+  *dw = {dwdt.i, -dwdt.r};
+}
+
+// Real part of W4 only (forward).
+__device__ __forceinline__ float w4_re(float x, float y) {
+  const float ax = fabsf(x), s = ax + y;
+  if (s >= 15.f) {
+    float x2 = x * x, y2 = y * y, A = 0.5f + y2;
+    float den = fmaf(x2, x2 + (2.f * y2 - 1.f), A * A);
+    return kInvSqrtPi * y * (A + x2) * frcp(den);
+  }
+  cplx w, dw;
+  w4_full(x, y, &w, &dw);
+  return w.r;
+}
+
+// ------------------------------------------------------------------ forward kernel
+struct __align__(16) LineC {
+  float pf, step, nfs, B1;     // fast: centre offset, step, -f*step, 2y^2-1 (Voigt) / gamma^2 (Lorentz)
+  float A2, K, KA, y;          // fast: A^2, K, K*A, y
+  int lo, hi, flags;           // window relative to the segment; bit0 skip, bit1 fast
+  float Kc;                    // amplitude for the general path
+};
+
+constexpr int kStageBytes = kStageLines * (16 + 8 + 4);
+constexpr int FLAG_SKIP = 1, FLAG_FAST = 2;
+
+template <int KIND>
+__device__ __forceinline__ void line_constants(const int4 p4, const float2 pr, const float is, const CondDev& cd,
+                                               int64_t i0, float dnu_f, double nu_min, double dnu, LineC& c) {
+  const int ic = p4.x;
+  const float f = __int_as_float(p4.y);
+  c.pf = (float)((int64_t)ic - i0);
+  int64_t lo = (int64_t)p4.z - i0, hi = (int64_t)p4.w - i0;
+  c.lo = (int)(lo < 0 ? 0 : lo);
+  c.hi = (int)(hi > kSeg - 1 ? kSeg - 1 : hi);
+  c.flags = is == 0.f ? FLAG_SKIP : 0;
+  const bool full = lo <= 0 && hi >= kSeg - 1;
+  // distance (grid steps) from the line centre to the nearest point of the segment
+  const float cen = c.pf + f;
+  const float dmin = fmaxf(0.f, fmaxf(cen - (float)(kSeg - 1), -cen));
+  if (KIND == PXC_LORENTZ) {
+    float g = pr.x * exp2f(pr.y * cd.log2_tratio) * cd.P_f;
+    c.step = dnu_f;
+    c.nfs = -f * dnu_f;
+    c.B1 = g * g;
+    c.Kc = is * g * kInvPi;
+    c.K = c.Kc;
+    c.A2 = 0.f; c.KA = 0.f; c.y = g;
+    if (full) c.flags |= FLAG_FAST;
+  } else {
+    float nu = (float)(nu_min + ((double)ic + (double)f) * dnu);
+    float alpha = KIND == PXC_GAUSS_HWHM ? cd.hwhm : cd.alpha_coef * nu;
+    float cc = kSqrtLn2 / alpha;             // 1 / (s sqrt 2)
+    if (KIND == PXC_VOIGT) {
+      float g = pr.x * exp2f(pr.y * cd.log2_tratio) * cd.P_f;
+      float y = g * cc;
+      c.y = y;
+      c.step = dnu_f * cc;
+      c.nfs = -f * c.step;
+      float A = 0.5f + y * y;
+      c.B1 = 2.f * y * y - 1.f;
+      c.A2 = A * A;
+      c.Kc = is * cc * kInvSqrtPi;
+      c.K = c.Kc * y * kInvSqrtPi;
+      c.KA = c.K * A;
+      if (full && dmin * c.step + y >= 15.f) c.flags |= FLAG_FAST;
+    } else {
+      // Gaussian: exp(-X^2) = 2^(-(X sqrt(log2 e))^2); scale x by sqrt(log2 e)
+      const float sl2e = 1.2011224087864498f;
+      c.step = dnu_f * cc * sl2e;
+      c.nfs = -f * c.step;
+      c.Kc = is * cc * kInvSqrtPi;
+      c.K = c.Kc;
+      c.y = 0.f; c.B1 = 0.f; c.A2 = 0.f; c.KA = 0.f;
+      // provably-zero trim: 2^(-t) with t > 159 is below the FP32 range of any product here
+      float reach = 12.7f / c.step;          // |X'| <= 12.7 <=> X^2 <= 111.8
+      float elo = ceilf(cen - reach), ehi = floorf(cen + reach);
+      if (elo > (float)c.lo) c.lo = (int)fminf(elo, (float)kSeg);
+      if (ehi < (float)c.hi) c.hi = (int)fmaxf(ehi, -1.f);
+      if (c.lo == 0 && c.hi == kSeg - 1 && full) c.flags |= FLAG_FAST;
+      if (c.lo > c.hi) c.flags |= FLAG_SKIP;
+    }
+  }
+}
+
+template <int KIND>
+__device__ __forceinline__ float eval_general(float x, const LineC& c) {
+  if (KIND == PXC_VOIGT) return c.Kc * w4_re(x, c.y);
+  if (KIND == PXC_LORENTZ) return c.K * frcp(fmaf(x, x, c.B1));
+  return c.K * fex2(-(x * x));
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kThreadsV, 2) k_profile(const ProfP p) {
+  __shared__ __align__(128) unsigned char raw[kStages][kStageBytes];
+  __shared__ LineC lc[kStageLines];
+  __shared__ __align__(8) uint64_t bar[kStages];
+  __shared__ Item item_sh;
+  __shared__ int abort_sh;
+
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int b = 0; b < kStages; ++b) mbar_init(&bar[b], 1);
+    fence_mbar_init();
+    abort_sh = 0;
+  }
+  __syncthreads();
+  unsigned phase = 0;  // bit b: parity to wait for on buffer b
+  const unsigned long long n_items = *p.n_items;
+  const float dnu_f = (float)p.dnu;
+
+  for (;;) {
+    if (tid == 0) {
+      unsigned long long it = atomicAdd(p.queue, 1ull);
+      if (it < n_items) item_sh = p.items[it]; else item_sh.cond = -1;
+    }
+    __syncthreads();
+    const Item item = item_sh;
+    if (item.cond < 0) break;
+    const CondDev cd = p.cond[item.cond];
+    const int64_t i0 = (int64_t)item.seg * kSeg;
+    const float* Is = p.Is + (int64_t)cd.slot * p.is_stride;
+    const int j0 = item.begin & ~3;
+    const int nst = item.end > item.begin ? (item.end - j0 + kStageLines - 1) / kStageLines : 0;
+
+    float sum[kPts], cmp[kPts];
+#pragma unroll
+    for (int q = 0; q < kPts; ++q) { sum[q] = 0.f; cmp[q] = 0.f; }
+
+    auto issue = [&](int st) {
+      const int b = st % kStages;
+      const int64_t J = (int64_t)j0 + (int64_t)st * kStageLines;
+      mbar_expect_tx(&bar[b], kStageBytes);
+      bulk_g2s(raw[b], p.pos + J, kStageLines * 16, &bar[b]);
+      bulk_g2s(raw[b] + kStageLines * 16, p.par + J, kStageLines * 8, &bar[b]);
+      bulk_g2s(raw[b] + kStageLines * 24, Is + J, kStageLines * 4, &bar[b]);
+    };
+    if (tid == 0) {
+      fence_proxy_async();
+      for (int st = 0; st < kStages && st < nst; ++st) issue(st);
+    }
+
+    bool aborted = false;
+    for (int st = 0; st < nst; ++st) {
+      const int b = st % kStages;
+      bool ok = mbar_wait_bounded(&bar[b], (phase >> b) & 1u, p.spin_limit);
+      phase ^= 1u << b;
+      if (__syncthreads_or(!ok)) { aborted = true; break; }
+      {
+        const int64_t J = (int64_t)j0 + (int64_t)st * kStageLines + tid;
+        const int4 p4 = reinterpret_cast<const int4*>(raw[b])[tid];
+        const float2 pr = reinterpret_cast<const float2*>(raw[b] + kStageLines * 16)[tid];
+        const float is = reinterpret_cast<const float*>(raw[b] + kStageLines * 24)[tid];
+        LineC c;
+        line_constants<KIND>(p4, pr, is, cd, i0, dnu_f, p.nu_min, p.dnu, c);
+        if (J < item.begin || J >= item.end) c.flags = FLAG_SKIP;
+        lc[tid] = c;
+      }
+      __syncthreads();
+      if (tid == 0 && st + kStages < nst) {
+        fence_proxy_async();
+        issue(st + kStages);
+      }
+      float acc[kPts];
+#pragma unroll
+      for (int q = 0; q < kPts; ++q) acc[q] = 0.f;
+      const float tf = (float)tid;
+      for (int l = 0; l < kStageLines; ++l) {
+        const LineC& c = lc[l];
+        const int flags = c.flags;
+        if (flags & FLAG_SKIP) continue;
+        if (flags & FLAG_FAST) {
+          const float x0 = fmaf(tf - c.pf, c.step, c.nfs);
+          const float s256 = 256.f * c.step;
+          if (KIND == PXC_VOIGT) {
+#pragma unroll
+            for (int q = 0; q < kPts; ++q) {
+              const float x = fmaf((float)q, s256, x0);
+              const float x2 = x * x;
+              const float den = fmaf(x2, x2 + c.B1, c.A2);
+              acc[q] = fmaf(fmaf(x2, c.K, c.KA), frcp(den), acc[q]);
+            }
+          } else if (KIND == PXC_LORENTZ) {
+#pragma unroll
+            for (int q = 0; q < kPts; ++q) {
+              const float x = fmaf((float)q, s256, x0);
+              acc[q] = fmaf(c.K, frcp(fmaf(x, x, c.B1)), acc[q]);
+            }
+          } else {
+#pragma unroll
+            for (int q = 0; q < kPts; ++q) {
+              const float x = fmaf((float)q, s256, x0);
+              acc[q] = fmaf(c.K, fex2(-(x * x)), acc[q]);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < kPts; ++q) {
+            const int li = tid + 256 * q;
+            if (li >= c.lo && li <= c.hi) {
+              const float x = fmaf((float)li - c.pf, c.step, c.nfs);
+              acc[q] += eval_general<KIND>(x, c);
+            }
+          }
+        }
+      }
+      // compensated fold of the stage sums (Knuth two-sum)
+#pragma unroll
+      for (int q = 0; q < kPts; ++q) {
+        float s = sum[q] + acc[q];
+        float bp = s - sum[q];
+        float err = (sum[q] - (s - bp)) + (acc[q] - bp);
+        sum[q] = s;
+        cmp[q] += err;
+      }
+      __syncthreads();
+    }
+    if (aborted) {
+      if (tid == 0) {
+        atomicOr(p.err, ERRB_TIMEOUT);
+        abort_sh = 1;
+      }
+      // let copies already in flight land before the CTA leaves (bounded again)
+      for (int b = 0; b < kStages; ++b) mbar_wait_bounded(&bar[b], (phase >> b) & 1u, p.spin_limit);
+      break;
+    }
+    // write the segment
+#pragma unroll
+    for (int q = 0; q < kPts; ++q) {
+      const int li = tid + 256 * q;
+      const int64_t i = i0 + li;
+      const float v = sum[q] + cmp[q];
+      if (item.slot < 0) {
+        if (i < p.n_grid) {
+          float* o = p.sigma + (int64_t)item.cond * p.n_grid + i;
+          if (p.accumulate) { if (nst) *o += v; } else *o = v;
+        }
+      } else {
+        p.partial[(int64_t)item.slot * kSeg + li] = v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+int profile_occupancy(int kind) {
+  int n = 0;
+  switch (kind) {
+    case PXC_GAUSS_DOPPLER: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_profile<PXC_GAUSS_DOPPLER>, kThreadsV, 0); break;
+    case PXC_GAUSS_HWHM: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_profile<PXC_GAUSS_HWHM>, kThreadsV, 0); break;
+    case PXC_LORENTZ: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_profile<PXC_LORENTZ>, kThreadsV, 0); break;
+    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_profile<PXC_VOIGT>, kThreadsV, 0); break;
+  }
+  return n > 0 ? n : 1;
+}
+
+void launch_profile(const ProfP& p, int grid_ctas, cudaStream_t s) {
+  switch (p.kind) {
+    case PXC_GAUSS_DOPPLER: k_profile<PXC_GAUSS_DOPPLER><<<grid_ctas, kThreadsV, 0, s>>>(p); break;
+    case PXC_GAUSS_HWHM: k_profile<PXC_GAUSS_HWHM><<<grid_ctas, kThreadsV, 0, s>>>(p); break;
+    case PXC_LORENTZ: k_profile<PXC_LORENTZ><<<grid_ctas, kThreadsV, 0, s>>>(p); break;
+    default: k_profile<PXC_VOIGT><<<grid_ctas, kThreadsV, 0, s>>>(p); break;
+  }
+  note_launches(1);
+}
+
+
+// ------------------------------------------------------------------ adjoint
+// One warp per sorted line: the lanes stride over the line's window, recompute the
+// profile and its width derivatives at each point and accumulate them against
+// w = dL/dsigma_s.  With G = sum w f, Da = sum w df/dalpha, Dg = sum w df/dgamma
+// (times the scaled intensity I_s) the chain rule gives
+//   dL/dA_l = I_s G / A_l,  dL/dgamma_ref_l = I_s (T_ref/T)^n P Dg,
+//   per-line shares of dL/dT (T_rot), dL/dT_vib and dL/dP (FP64, reduced in a fixed order).
+// Voigt: f = (c/sqrt(pi)) Re w(z), z = (x + i gamma) c, c = sqrt(ln2)/alpha, with
+//   df/dgamma = -(c^2/sqrt(pi)) Im w'(z),  df/dalpha = -(c/(alpha sqrt(pi))) (Re w + Re(z w'(z))).
+template <int KIND>
+__global__ void __launch_bounds__(256) k_adjoint(const AdjP p) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n = (int64_t)*p.n_dev;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const float dnu_f = (float)p.dnu;
+  for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < n; j += warps) {
+    const int4 p4 = p.pos[j];
+    const float2 pr = p.par[j];
+    const float is = p.Is[j];
+    const int ic = p4.x;
+    const float f = __int_as_float(p4.y);
+    const float nu_f = (float)(p.nu_min + ((double)ic + (double)f) * p.dnu);
+    const float alpha = KIND == PXC_GAUSS_HWHM ? p.cond.hwhm : p.cond.alpha_coef * nu_f;
+    const float gfac = exp2f(pr.y * p.cond.log2_tratio) * p.cond.P_f;   // dgamma/dgamma_ref
+    const float gam = (KIND == PXC_LORENTZ || KIND == PXC_VOIGT) ? pr.x * gfac : 0.f;
+    const float cc = kSqrtLn2 / alpha;
+    float g0 = 0.f, ga = 0.f, gg = 0.f;
+    if (is != 0.f) {
+      for (int i = p4.z + lane; i <= p4.w; i += 32) {
+        const float wi = p.w[i];
+        const float x = ((float)(i - ic) - f) * dnu_f;
+        if (KIND == PXC_VOIGT) {
+          const float X = x * cc, Y = gam * cc;
+          cplx w, dw;
+          w4_full(X, Y, &w, &dw);
+          g0 = fmaf(wi, w.r, g0);
+          gg = fmaf(wi, dw.i, gg);
+          ga = fmaf(wi, w.r + (X * dw.r - Y * dw.i), ga);
+        } else if (KIND == PXC_LORENTZ) {
+          const float x2 = x * x, g2 = gam * gam;
+          const float d = 1.f / (x2 + g2);
+          g0 = fmaf(wi, d, g0);
+          gg = fmaf(wi, (x2 - g2) * d * d, gg);
+        } else {
+          const float X = x * cc;
+          const float e = expf(-X * X);
+          g0 = fmaf(wi, e, g0);
+          ga = fmaf(wi, e * X * X, ga);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      g0 += __shfl_down_sync(0xffffffffu, g0, o);
+      ga += __shfl_down_sync(0xffffffffu, ga, o);
+      gg += __shfl_down_sync(0xffffffffu, gg, o);
+    }
+    if (lane == 0) {
+      const uint32_t t = p.sidx[j];
+      double G = 0.0, Da = 0.0, Dg = 0.0;
+      const double ccd = cc, ad = alpha, spi = 1.7724538509055160273;
+      if (KIND == PXC_VOIGT) {
+        G = ccd / spi * g0;
+        Dg = -(ccd * ccd / spi) * gg;
+        Da = -(ccd / (ad * spi)) * ga;
+      } else if (KIND == PXC_LORENTZ) {
+        G = (double)gam / kPi * g0;
+        Dg = gg / kPi;
+      } else {
+        G = ccd / spi * g0;
+        Da = ccd / spi * (-(double)g0 + 2.0 * ga) / ad;
+      }
+      const double I = is;
+      const double A = p.sA[j];
+      if (p.dA) p.dA[t] = (float)(I * G / A);
+      if (p.dgref) p.dgref[t] = (float)(I * (double)gfac * Dg);
+      const int32_t u = p.su[j], l = p.sl[j];
+      const double Eu = p.srec[u].x, El = p.srec[l].x;
+      const double c2 = p.c2, T = p.T;
+      const double Q = p.qres[0], dQ = p.qres[1], dQv = p.qres[2];
+      double dlnT, dlnTv = 0.0;
+      if (p.T_vib > 0.0) {
+        const double evl = p.E_vib[l], evu = p.E_vib[u];
+        const double erl = El - evl, eru = Eu - evu;
+        const double nv = evu - evl, nr = eru - erl;
+        const double X = c2 * (nv / p.T_vib + nr / T);
+        const double st = 1.0 / expm1(X);
+        dlnT = c2 * erl / (T * T) - c2 * nr / (T * T) * st - dQ / Q;
+        dlnTv = c2 * evl / (p.T_vib * p.T_vib) - c2 * nv / (p.T_vib * p.T_vib) * st - dQv / Q;
+      } else {
+        const double nu = Eu - El;
+        const double st = 1.0 / expm1(c2 * nu / T);
+        dlnT = c2 * El / (T * T) - c2 * nu / (T * T) * st - dQ / Q;
+      }
+      const bool dop = KIND == PXC_GAUSS_DOPPLER || KIND == PXC_VOIGT;
+      const bool pres = KIND == PXC_LORENTZ || KIND == PXC_VOIGT;
+      const double dadT = dop ? ad / (2.0 * T) : 0.0;
+      const double dgdT = pres ? -(double)pr.y * (double)gam / T : 0.0;
+      const double dgdP = pres ? (double)gam / p.P : 0.0;
+      p.lineT[j] = I * (dlnT * G + dadT * Da + dgdT * Dg);
+      p.lineTv[j] = I * dlnTv * G;
+      p.lineP[j] = I * dgdP * Dg;
+    }
+  }
+}
+
+void launch_adjoint(const AdjP& p, cudaStream_t s) {
+  int64_t blocks = (p.n_max * 32 + 255) / 256;
+  if (blocks > 148 * 8) blocks = 148 * 8;
+  if (blocks < 1) blocks = 1;
+  switch (p.kind) {
+    case PXC_GAUSS_DOPPLER: k_adjoint<PXC_GAUSS_DOPPLER><<<(unsigned)blocks, 256, 0, s>>>(p); break;
+    case PXC_GAUSS_HWHM: k_adjoint<PXC_GAUSS_HWHM><<<(unsigned)blocks, 256, 0, s>>>(p); break;
+    case PXC_LORENTZ: k_adjoint<PXC_LORENTZ><<<(unsigned)blocks, 256, 0, s>>>(p); break;
+    default: k_adjoint<PXC_VOIGT><<<(unsigned)blocks, 256, 0, s>>>(p); break;
+  }
+  note_launches(1);
+}
+
+// Fixed-order FP64 reduction of the per-line scalar shares (one CTA).
+__global__ void k_adjoint_reduce(const double* __restrict__ a, const double* __restrict__ b,
+                                 const double* __restrict__ c, const unsigned long long* __restrict__ n_dev,
+                                 double* oa, double* ob, double* oc) {
+  __shared__ double r[3][1024];
+  const int64_t n = (int64_t)*n_dev;
+  int64_t per = (n + blockDim.x - 1) / blockDim.x;
+  int64_t lo = threadIdx.x * per, hi = lo + per < n ? lo + per : n;
+  double sa = 0, sb = 0, sc = 0;
+  for (int64_t i = lo; i < hi; ++i) { sa += a[i]; sb += b[i]; sc += c[i]; }
+  r[0][threadIdx.x] = sa; r[1][threadIdx.x] = sb; r[2][threadIdx.x] = sc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      r[0][threadIdx.x] += r[0][threadIdx.x + o];
+      r[1][threadIdx.x] += r[1][threadIdx.x + o];
+      r[2][threadIdx.x] += r[2][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (oa) *oa = r[0][0];
+    if (ob) *ob = r[1][0];
+    if (oc) *oc = r[2][0];
+  }
+}
+
+void launch_adjoint_reduce(const double* lineT, const double* lineTv, const double* lineP,
+                           const unsigned long long* n_dev, int64_t n_max, double* outT, double* outTv,
+                           double* outP, cudaStream_t s) {
+  (void)n_max;
+  k_adjoint_reduce<<<1, 1024, 0, s>>>(lineT, lineTv, lineP, n_dev, outT, outTv, outP);
+  note_launches(1);
+}
+
+}  // namespace pxc

@@ -1,0 +1,83 @@
+"""CPU-side checks of the C-ABI library: it builds for sm_103a, loads, exports every
+function include/pxc.h declares, and its host-only argument checks work without a GPU."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pxc.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pxc_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2609_17273_b300 import build
+    path = build.build()
+    return ctypes.CDLL(path), path
+
+
+def test_library_exports_every_declared_function(lib):
+    L, path = lib
+    names = _declared()
+    assert "pxc_cross_section" in names and "pxc_partition_function" in names
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (pxc_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, f"declared but not exported: {missing}"
+    for n in names:
+        getattr(L, n)
+
+
+def test_binding_names_match_header():
+    import paper_2609_17273_b300 as pxc
+    assert sorted(pxc.ABI_FUNCTIONS) == _declared()
+
+
+def test_host_side_argument_checks_without_gpu(lib):
+    import paper_2609_17273_b300 as pxc
+    L = pxc.load()
+    cap = pxc.pxc_capacity(1000, 1000, 5000, 1, 0)
+    nb = ctypes.c_size_t()
+    assert L.pxc_workspace_query(ctypes.byref(cap), ctypes.byref(nb)) == 0
+    assert nb.value > 1000 * 50
+    bad = pxc.pxc_capacity(-1, 1000, 5000, 1, 0)
+    assert L.pxc_workspace_query(ctypes.byref(bad), ctypes.byref(nb)) == 1
+    assert b"bad capacity" in L.pxc_last_error()
+    h = ctypes.c_void_p()
+    # null scratch buffer is rejected before any CUDA call
+    assert L.pxc_workspace_create(ctypes.byref(cap), None, nb.value, ctypes.byref(h)) == 1
+    # misaligned buffer
+    assert L.pxc_workspace_create(ctypes.byref(cap), ctypes.c_void_p(0x1001), nb.value, ctypes.byref(h)) == 1
+    assert L.pxc_stream_buffer_bytes(1000, 1, 1) >= 1000 * 20
+
+
+def test_workspace_grows_linearly_with_lines(lib):
+    import paper_2609_17273_b300 as pxc
+    L = pxc.load()
+    sizes = []
+    for n in (10**6, 2 * 10**6):
+        cap = pxc.pxc_capacity(10**5, n, 10**6, 1, 0)
+        nb = ctypes.c_size_t()
+        assert L.pxc_workspace_query(ctypes.byref(cap), ctypes.byref(nb)) == 0
+        sizes.append(nb.value)
+    per_line = (sizes[1] - sizes[0]) / 1e6
+    assert 60 < per_line < 200, per_line
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    import paper_2609_17273_b300 as pxc
+    saved = pxc._lib
+    pxc._lib = None
+    try:
+        with pytest.raises(ImportError):
+            pxc.load(str(tmp_path / "missing.so"))
+    finally:
+        pxc._lib = saved
