@@ -60,7 +60,7 @@ void launch_segments(const int4* pos, const unsigned long long* n_dev, int64_t n
                      cudaStream_t s);
 
 void launch_items(const int32_t* segr, int64_t nseg, int n_c, int item_lines, int32_t* seg_items,
-                  Item* items, unsigned long long* counters, cudaStream_t s);
+                  Item* items, unsigned long long* counters, int64_t max_items, cudaStream_t s);
 
 void launch_reduce_partials(const Item* items, const int32_t* seg_items, int64_t nseg, int n_c,
                             const float* partial, float* sigma, int64_t n_grid, cudaStream_t s);

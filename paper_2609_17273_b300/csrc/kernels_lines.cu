@@ -454,7 +454,7 @@ __global__ void __launch_bounds__(256) k_prepare(const uint64_t* __restrict__ sk
     double fc = floor(c);
     float f = (float)__dsub_rn(c, fc);
     pos[j] = make_int4((int)fc, __float_as_int(f), (int)a, (int)b);
-    par[j] = gref ? make_float2(gref[t], nT[t]) : make_float2(0.f, 0.f);
+    par[j] = (gref && nT) ? make_float2(gref[t], nT[t]) : make_float2(0.f, 0.f);
     unsigned long long wsz = (unsigned long long)(b - a + 1);
     ev += wsz;
     if (Iv) {
@@ -462,7 +462,7 @@ __global__ void __launch_bounds__(256) k_prepare(const uint64_t* __restrict__ sk
       Is[j] = is;
       if (is != 0.f) { evnz += wsz; ++nz; }
     }
-    if (su) {
+    if (su && up) {
       su[j] = up[t];
       sl[j] = lo[t];
       sA[j] = A32 ? (double)((const float*)Av)[t] : ((const double*)Av)[t];
@@ -485,6 +485,7 @@ void launch_prepare(const uint64_t* skey, const uint32_t* sidx, const unsigned l
   if (n_max == 0) return;
   int64_t blocks = (n_max + 255) / 256;
   if (blocks > 148 * 16) blocks = 148 * 16;
+  if (!gather_tr) su = nullptr, sl = nullptr, sA = nullptr;  // no transition arrays: nothing to gather
   k_prepare<<<(unsigned)blocks, 256, 0, s>>>(skey, sidx, n_dev, gp, gamma_ref, n_T, Iv, kexp, pos, par, Is,
                                             gather_tr ? gather_tr->upper : nullptr,
                                             gather_tr ? gather_tr->lower : nullptr,
@@ -584,7 +585,7 @@ void launch_segments(const int4* pos, const unsigned long long* n_dev, int64_t n
 // Work items: each (condition, segment) group is split into ceil(lines / item_lines) items (at least one).
 __global__ void k_items(const int32_t* __restrict__ segr, int64_t nseg, int n_c, int item_lines,
                         int32_t* __restrict__ seg_items, Item* __restrict__ items,
-                        unsigned long long* __restrict__ counters) {
+                        unsigned long long* __restrict__ counters, int64_t max_items) {
   __shared__ unsigned long long part[1024];
   const int64_t ng = nseg * n_c;
   int64_t per = (ng + blockDim.x - 1) / blockDim.x;
@@ -603,7 +604,7 @@ __global__ void k_items(const int32_t* __restrict__ segr, int64_t nseg, int n_c,
     unsigned long long run = 0;
     for (int i = 0; i < (int)blockDim.x; ++i) { unsigned long long v = part[i]; part[i] = run; run += v; }
     seg_items[ng] = (int32_t)run;
-    counters[CNT_ITEMS] = run;
+    counters[CNT_ITEMS] = run < (unsigned long long)max_items ? run : (unsigned long long)max_items;
     counters[CNT_QUEUE] = 0;
   }
   __syncthreads();
@@ -622,6 +623,7 @@ __global__ void k_items(const int32_t* __restrict__ segr, int64_t nseg, int n_c,
       it.end = (int32_t)(en < e ? en : e);
       if (it.begin > e) it.begin = e;
       int64_t idx = (int64_t)run + k;
+      if (idx >= max_items) break;  // sized on the host; never taken for calls that passed the capacity check
       it.slot = k == 0 ? -1 : (int32_t)(idx - gi - 1);
       it.first_of_seg = (int32_t)run;
       it.n_of_seg = (int32_t)c;
@@ -633,8 +635,8 @@ __global__ void k_items(const int32_t* __restrict__ segr, int64_t nseg, int n_c,
 }
 
 void launch_items(const int32_t* segr, int64_t nseg, int n_c, int item_lines, int32_t* seg_items, Item* items,
-                  unsigned long long* counters, cudaStream_t s) {
-  k_items<<<1, 1024, 0, s>>>(segr, nseg, n_c, item_lines, seg_items, items, counters);
+                  unsigned long long* counters, int64_t max_items, cudaStream_t s) {
+  k_items<<<1, 1024, 0, s>>>(segr, nseg, n_c, item_lines, seg_items, items, counters, max_items);
   note_launches(1);
 }
 

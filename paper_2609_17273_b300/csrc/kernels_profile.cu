@@ -187,6 +187,12 @@ struct __align__(16) LineC {
 };
 
 constexpr int kStageBytes = kStageLines * (16 + 8 + 4);
+// Smallest Doppler HWHM used (cm^-1).  Keeps the scaled FP32 arithmetic finite for lines with
+// nu below ~0.05 cm^-1, whose true alpha is far below both the grid step and gamma: the
+// sampled profile changes by less than (alpha/gamma)^2 off the line centre.
+constexpr float kAlphaMin = 8.4e-8f;
+// Smallest Lorentz HWHM used (cm^-1): gamma^2 stays a normal FP32 number.
+constexpr float kGammaMin = 1e-15f;
 constexpr int FLAG_SKIP = 1, FLAG_FAST = 2;
 
 template <int KIND>
@@ -204,7 +210,7 @@ __device__ __forceinline__ void line_constants(const int4 p4, const float2 pr, c
   const float cen = c.pf + f;
   const float dmin = fmaxf(0.f, fmaxf(cen - (float)(kSeg - 1), -cen));
   if (KIND == PXC_LORENTZ) {
-    float g = pr.x * exp2f(pr.y * cd.log2_tratio) * cd.P_f;
+    float g = fmaxf(pr.x * exp2f(pr.y * cd.log2_tratio) * cd.P_f, kGammaMin);
     c.step = dnu_f;
     c.nfs = -f * dnu_f;
     c.B1 = g * g;
@@ -214,7 +220,7 @@ __device__ __forceinline__ void line_constants(const int4 p4, const float2 pr, c
     if (full) c.flags |= FLAG_FAST;
   } else {
     float nu = (float)(nu_min + ((double)ic + (double)f) * dnu);
-    float alpha = KIND == PXC_GAUSS_HWHM ? cd.hwhm : cd.alpha_coef * nu;
+    float alpha = fmaxf(KIND == PXC_GAUSS_HWHM ? cd.hwhm : cd.alpha_coef * nu, kAlphaMin);
     float cc = kSqrtLn2 / alpha;             // 1 / (s sqrt 2)
     if (KIND == PXC_VOIGT) {
       float g = pr.x * exp2f(pr.y * cd.log2_tratio) * cd.P_f;
@@ -452,9 +458,9 @@ __global__ void __launch_bounds__(256) k_adjoint(const AdjP p) {
     const int ic = p4.x;
     const float f = __int_as_float(p4.y);
     const float nu_f = (float)(p.nu_min + ((double)ic + (double)f) * p.dnu);
-    const float alpha = KIND == PXC_GAUSS_HWHM ? p.cond.hwhm : p.cond.alpha_coef * nu_f;
+    const float alpha = fmaxf(KIND == PXC_GAUSS_HWHM ? p.cond.hwhm : p.cond.alpha_coef * nu_f, kAlphaMin);
     const float gfac = exp2f(pr.y * p.cond.log2_tratio) * p.cond.P_f;   // dgamma/dgamma_ref
-    const float gam = (KIND == PXC_LORENTZ || KIND == PXC_VOIGT) ? pr.x * gfac : 0.f;
+    const float gam = KIND == PXC_LORENTZ ? fmaxf(pr.x * gfac, kGammaMin) : KIND == PXC_VOIGT ? pr.x * gfac : 0.f;
     const float cc = kSqrtLn2 / alpha;
     float g0 = 0.f, ga = 0.f, gg = 0.f;
     if (is != 0.f) {

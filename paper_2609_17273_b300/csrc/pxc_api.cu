@@ -239,6 +239,7 @@ pxc_status check_prof(const pxc_profile_args* pa, const pxc_transitions* tr) {
     return fail(PXC_ERR_ARG, "profile: gamma_ref and n_T required");
   if ((pa->kind == PXC_LORENTZ || pa->kind == PXC_VOIGT) && !(pa->T_ref > 0.0))
     return fail(PXC_ERR_ARG, "profile: T_ref must be > 0");
+  if (!(pa->cutoff >= 0.0)) return fail(PXC_ERR_ARG, "profile: cutoff must be >= 0");
   return PXC_OK;
 }
 
@@ -463,8 +464,11 @@ pxc_status pxc_cross_section(pxc_workspace* ws, const pxc_states* st, const pxc_
   if ((r = check_states(st)) || (r = check_trans(tr)) || (r = check_prof(pa, tr))) return r;
   if ((r = check_grid(grid, pa->cutoff))) return r;
   if (!(threshold >= 0.0)) return fail(PXC_ERR_ARG, "threshold must be >= 0");
-  for (int i = 0; i < n_c; ++i)
+  for (int i = 0; i < n_c; ++i) {
     if ((r = check_cond(c[i], false, st))) return r;
+    if (pa->kind == PXC_LORENTZ && !(c[i].P > 0.0)) return fail(PXC_ERR_ARG, "Lorentzian profile needs P > 0");
+    if (!(c[i].P >= 0.0)) return fail(PXC_ERR_ARG, "condition: P must be >= 0");
+  }
   WsExtra* x = X(ws);
   const Layout& L = x->L;
   if (tr->n > ws->cap.max_lines || st->n > ws->cap.max_states || grid->n > std::max<int64_t>(ws->cap.max_grid, 1) ||
@@ -532,7 +536,7 @@ pxc_status pxc_cross_section(pxc_workspace* ws, const pxc_states* st, const pxc_
   }
   launch_segments(at<int4>(ws, L.pos), cnt + CNT_KEPT, nseg, at<int32_t>(ws, L.segr), s);
   launch_items(at<int32_t>(ws, L.segr), nseg, n_c, n_c == 1 ? kItemLines : INT32_MAX / 2, at<int32_t>(ws, L.seg_items),
-               at<Item>(ws, L.items), cnt, s);
+               at<Item>(ws, L.items), cnt, L.max_items, s);
   ProfP p{};
   p.pos = at<int4>(ws, L.pos);
   p.par = at<float2>(ws, L.par);
