@@ -23,7 +23,20 @@ struct SlotP {                    // one temperature pair
 };
 
 void launch_boltzmann(const pxc_states* st, const SlotP* slots_dev, int nslot, double2* srec, int64_t srec_stride,
-                      double* qpart, double* qres, unsigned* err, cudaStream_t s);
+                      StateFast* sfast, double* qpart, double* qres, unsigned* err, cudaStream_t s);
+
+struct BoundP {
+  float log2_thr;
+  float log2_invQ;
+  float c2_T;
+  int lte;
+};
+void launch_lines_compact(const pxc_transitions* tr, int64_t ns, const StateFast* sfast, const double2* srec,
+                          const double* qres, const GridP& gp, double threshold, const BoundP& bp, int with_I,
+                          uint64_t* kstage, uint32_t* istage, double* Iv, uint32_t* bcount, int64_t nblk,
+                          unsigned long long* maxbits, unsigned* err, cudaStream_t s);
+void launch_compact_staged(const uint64_t* kstage, const uint32_t* istage, const uint32_t* boff, int64_t nblk,
+                           uint64_t* okey, uint32_t* oidx, cudaStream_t s);
 
 void launch_lines(const pxc_transitions* tr, const int32_t* g, int64_t ns, const double2* srec,
                   const double* qres, const GridP& gp, int use_grid, double threshold, int with_intensity,
@@ -60,7 +73,8 @@ void launch_segments(const int4* pos, const unsigned long long* n_dev, int64_t n
                      cudaStream_t s);
 
 void launch_items(const int32_t* segr, int64_t nseg, int n_c, int item_lines, int32_t* seg_items,
-                  Item* items, unsigned long long* counters, int64_t max_items, cudaStream_t s);
+                  Item* items, unsigned long long* counters, int64_t max_items, int64_t target_items,
+                  int64_t max_partial, cudaStream_t s);
 
 void launch_reduce_partials(const Item* items, const int32_t* seg_items, int64_t nseg, int n_c,
                             const float* partial, float* sigma, int64_t n_grid, cudaStream_t s);

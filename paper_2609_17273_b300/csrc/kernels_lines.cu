@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(kThreadsQ) k_boltzmann(const double* __restric
                                                          const double* __restrict__ Ev, int64_t n,
                                                          const SlotP* __restrict__ slots, int nslot,
                                                          double2* __restrict__ srec, int64_t stride,
+                                                         StateFast* __restrict__ sfast,
                                                          double* __restrict__ qpart, unsigned* err) {
   __shared__ double red[kThreadsQ / 32][3];
   for (int sl = 0; sl < nslot; ++sl) {
@@ -58,7 +59,7 @@ __global__ void __launch_bounds__(kThreadsQ) k_boltzmann(const double* __restric
     unsigned bad = 0;
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
       double e = E[s];
-      double b = 0.0;
+      double b = 0.0, lb = -INFINITY;
       if (isnan(e)) {
         b = 0.0;
       } else if (isinf(e)) {
@@ -77,6 +78,7 @@ __global__ void __launch_bounds__(kThreadsQ) k_boltzmann(const double* __restric
           bad |= ERRB_OVERFLOW;
         } else {
           b = exp(x);
+          lb = x * 1.4426950408889634;
           double term = (double)g[s] * b;
           q0 += term;
           q1 += term * er * sp.c2_T;   // divided by T in k_qfinal: dQ/dT = sum g b c2 E_rot / T^2
@@ -84,6 +86,13 @@ __global__ void __launch_bounds__(kThreadsQ) k_boltzmann(const double* __restric
         }
       }
       if (srec) srec[(int64_t)sl * stride + s] = make_double2(e, b);
+      if (sfast) {
+        StateFast r;
+        r.E = e;
+        r.g = g[s];
+        r.lb = (float)lb;
+        sfast[s] = r;
+      }
     }
     if (bad) set_err(err, bad);
     // moments: dQ/dT = sum term c2 E_rot / T^2 = (sum term E_rot c2/T) / T
@@ -127,9 +136,9 @@ __global__ void k_qfinal(const double* __restrict__ qpart, int nblk, int nslot, 
 }
 
 void launch_boltzmann(const pxc_states* st, const SlotP* slots_dev, int nslot, double2* srec, int64_t srec_stride,
-                      double* qpart, double* qres, unsigned* err, cudaStream_t s) {
+                      StateFast* sfast, double* qpart, double* qres, unsigned* err, cudaStream_t s) {
   k_boltzmann<<<kQBlocks, kThreadsQ, 0, s>>>(st->E, st->g, st->E_vib, st->n, slots_dev, nslot, srec, srec_stride,
-                                             qpart, err);
+                                             sfast, qpart, err);
   k_qfinal<<<nslot, 1024, 0, s>>>(qpart, kQBlocks, nslot, slots_dev, qres);
   note_launches(2);
 }
@@ -221,6 +230,167 @@ void launch_lines(const pxc_transitions* tr, const int32_t* g, int64_t ns, const
   note_launches(1);
 }
 
+// ------------------------------------------------------------------ K-I, compacting form (cross sections)
+// Same selection as k_lines, but kept lines are written compacted per block in index order
+// (key, index) and I by transition index; rejected lines write nothing.  With a threshold,
+// a conservative FP32 upper bound on |I| rejects lines without touching the FP64 Boltzmann
+// table or dividing: |I| <= g_u A max(b_l, b_u) m / (8 pi c Q nu^2), m = min(1, c2 nu/T) for
+// LTE (b_l - b_u = b_l (1 - e^{-c2 nu/T})) and m = 1 for two temperatures, evaluated in log2
+// units with a 1e-3 margin that covers every FP32 rounding in it.
+
+
+// Block-wide exclusive rank of `flag` among the 256 threads in thread order, and the total.
+__device__ __forceinline__ uint32_t block_rank(bool flag, uint32_t* wsum, uint32_t* total) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned m = __ballot_sync(0xffffffffu, flag);
+  if (lane == 0) wsum[w] = __popc(m);
+  __syncthreads();
+  uint32_t before = 0, tot = 0;
+#pragma unroll
+  for (int i = 0; i < kThreadsI / 32; ++i) { before += i < w ? wsum[i] : 0u; tot += wsum[i]; }
+  __syncthreads();
+  *total = tot;
+  return before + __popc(m & ((1u << lane) - 1u));
+}
+
+__global__ void __launch_bounds__(kThreadsI) k_lines_c(const int32_t* __restrict__ up, const int32_t* __restrict__ lo,
+                                                       const void* __restrict__ Av, int A32, int64_t n,
+                                                       const StateFast* __restrict__ sfast,
+                                                       const double2* __restrict__ srec, int64_t ns,
+                                                       const double* __restrict__ qres, GridP gp, double threshold,
+                                                       BoundP bp, int with_I, uint64_t* __restrict__ kstage,
+                                                       uint32_t* __restrict__ istage, double* __restrict__ Iv,
+                                                       uint32_t* __restrict__ bcount,
+                                                       unsigned long long* __restrict__ maxbits, unsigned* err) {
+  __shared__ uint32_t wsum[kThreadsI / 32];
+  // candidates of one round for the exact FP64 test, packed so the FP64 work runs on dense warps
+  __shared__ uint32_t c_t[kThreadsI];
+  __shared__ int32_t c_u[kThreadsI], c_l[kThreadsI], c_g[kThreadsI];
+  __shared__ double c_nu[kThreadsI], c_A[kThreadsI];
+  const double invQ = with_I ? qres[3] : 0.0;
+  const float l2invQ = with_I ? (float)log2(invQ) : 0.f;
+  const int64_t base = (int64_t)blockIdx.x * kLinesPerBlockI;
+  const long long lo_bits = __double_as_longlong(gp.nu_keep_lo), hi_bits = __double_as_longlong(gp.nu_keep_hi);
+  const int lane = threadIdx.x & 31;
+  uint32_t run = 0;
+  unsigned long long mx = 0;
+  unsigned bad = 0;
+  for (int k = 0; k < kLinesPerBlockI / kThreadsI; ++k) {
+    const int64_t t = base + k * kThreadsI + threadIdx.x;
+    bool keep = false;
+    double nu = 0.0, A = 0.0;
+    int32_t u = 0, l = 0, g = 0;
+    if (t < n) {
+      u = up[t];
+      l = lo[t];
+      A = A32 ? (double)((const float*)Av)[t] : ((const double*)Av)[t];
+      if (u < 0 || u >= ns || l < 0 || l >= ns) {
+        bad |= ERRB_ID;
+      } else {
+        if (!isfinite(A)) bad |= ERRB_NONFINITE;
+        const StateFast fu = sfast[u], fl = sfast[l];
+        g = fu.g;
+        nu = __dsub_rn(fu.E, fl.E);
+        if (gp.exact_bounds) {
+          const long long nb = __double_as_longlong(nu);
+          keep = nb >= lo_bits && nb <= hi_bits;
+        } else {
+          int64_t a, b;
+          keep = nu > 0.0 && exact_window(nu, gp, &a, &b);
+        }
+        if (keep && with_I && threshold > 0.0) {
+          const float nuf = (float)nu;
+          const float m = bp.lte ? fminf(1.f, bp.c2_T * nuf) : 1.f;
+          const float P = (float)g * (float)A * m / (nuf * nuf);
+          if (__log2f(P) + fmaxf(fu.lb, fl.lb) + l2invQ < bp.log2_thr) keep = false;
+        }
+      }
+    }
+    uint32_t tot;
+    if (!with_I) {
+      const uint32_t r = block_rank(keep, wsum, &tot);
+      if (keep) {
+        kstage[base + run + r] = (uint64_t)__double_as_longlong(nu);
+        istage[base + run + r] = (uint32_t)t;
+      }
+      run += tot;
+      continue;
+    }
+    // pack the candidates of this round (index order) ...
+    const uint32_t r = block_rank(keep, wsum, &tot);
+    if (keep) {
+      c_t[r] = (uint32_t)t; c_u[r] = u; c_l[r] = l; c_g[r] = g; c_nu[r] = nu; c_A[r] = A;
+    }
+    __syncthreads();
+    // ... and run the exact test on the first `tot` threads
+    bool kept = false;
+    double I = 0.0;
+    uint32_t tt = 0;
+    if (threadIdx.x < tot) {
+      tt = c_t[threadIdx.x];
+      const double nuc = c_nu[threadIdx.x];
+      const double num = (double)c_g[threadIdx.x] * c_A[threadIdx.x] * invQ *
+                         (srec[c_l[threadIdx.x]].y - srec[c_u[threadIdx.x]].y);
+      const double den = nuc * nuc;
+      kept = fabs(num) >= threshold * den;
+      if (kept) I = num / den;
+      nu = nuc;
+    }
+    uint32_t tot2;
+    const uint32_t r2 = block_rank(kept, wsum, &tot2);
+    if (kept) {
+      kstage[base + run + r2] = (uint64_t)__double_as_longlong(nu);
+      istage[base + run + r2] = tt;
+      Iv[tt] = I;
+      const unsigned long long ib = (unsigned long long)__double_as_longlong(fabs(I));
+      mx = ib > mx ? ib : mx;
+    }
+    run += tot2;
+  }
+  if (bad) set_err(err, bad);
+  if (with_I) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long v = __shfl_down_sync(0xffffffffu, mx, o);
+      mx = v > mx ? v : mx;
+    }
+    if (lane == 0 && mx) atomicMax(maxbits, mx);
+  }
+  if (threadIdx.x == 0) bcount[blockIdx.x] = run;
+}
+
+void launch_lines_compact(const pxc_transitions* tr, int64_t ns, const StateFast* sfast, const double2* srec,
+                          const double* qres, const GridP& gp, double threshold, const BoundP& bp, int with_I,
+                          uint64_t* kstage, uint32_t* istage, double* Iv, uint32_t* bcount, int64_t nblk,
+                          unsigned long long* maxbits, unsigned* err, cudaStream_t s) {
+  if (nblk == 0) return;
+  k_lines_c<<<(unsigned)nblk, kThreadsI, 0, s>>>(tr->upper, tr->lower, tr->A, tr->A_is_f32, tr->n, sfast, srec, ns,
+                                                 qres, gp, threshold, bp, with_I, kstage, istage, Iv, bcount,
+                                                 maxbits, err);
+  note_launches(1);
+}
+
+// Copies each block's staged kept lines to its offset (exclusive scan of the counts, total at [nblk]).
+__global__ void __launch_bounds__(256) k_compact_staged(const uint64_t* __restrict__ kstage,
+                                                        const uint32_t* __restrict__ istage,
+                                                        const uint32_t* __restrict__ boff, uint64_t* __restrict__ okey,
+                                                        uint32_t* __restrict__ oidx) {
+  const int64_t b = blockIdx.x;
+  const uint32_t off = boff[b], cnt = boff[b + 1] - off;
+  const int64_t base = b * kLinesPerBlockI;
+  for (uint32_t r = threadIdx.x; r < cnt; r += blockDim.x) {
+    okey[off + r] = kstage[base + r];
+    oidx[off + r] = istage[base + r];
+  }
+}
+
+void launch_compact_staged(const uint64_t* kstage, const uint32_t* istage, const uint32_t* boff, int64_t nblk,
+                           uint64_t* okey, uint32_t* oidx, cudaStream_t s) {
+  if (nblk == 0) return;
+  k_compact_staged<<<(unsigned)nblk, 256, 0, s>>>(kstage, istage, boff, okey, oidx);
+  note_launches(1);
+}
+
 // ------------------------------------------------------------------ exclusive scan of block counts (one CTA)
 __global__ void k_scan_counts(uint32_t* __restrict__ c, int64_t n, unsigned long long* total) {
   __shared__ unsigned long long part[1024];
@@ -234,6 +404,7 @@ __global__ void k_scan_counts(uint32_t* __restrict__ c, int64_t n, unsigned long
     unsigned long long run = 0;
     for (int i = 0; i < (int)blockDim.x; ++i) { unsigned long long v = part[i]; part[i] = run; run += v; }
     *total = run;
+    c[n] = (uint32_t)run;
   }
   __syncthreads();
   unsigned long long run = part[threadIdx.x];
@@ -583,13 +754,42 @@ void launch_segments(const int4* pos, const unsigned long long* n_dev, int64_t n
 }
 
 // Work items: each (condition, segment) group is split into ceil(lines / item_lines) items (at least one).
-__global__ void k_items(const int32_t* __restrict__ segr, int64_t nseg, int n_c, int item_lines,
+__global__ void k_items(const int32_t* __restrict__ segr, int64_t nseg, int n_c, int item_lines_max,
                         int32_t* __restrict__ seg_items, Item* __restrict__ items,
-                        unsigned long long* __restrict__ counters, int64_t max_items) {
+                        unsigned long long* __restrict__ counters, int64_t max_items, int64_t target_items,
+                        int64_t max_partial) {
   __shared__ unsigned long long part[1024];
+  __shared__ int item_lines_sh;
   const int64_t ng = nseg * n_c;
   int64_t per = (ng + blockDim.x - 1) / blockDim.x;
   int64_t a = threadIdx.x * per, b = a + per < ng ? a + per : ng;
+  // Lines per item: about target_items equal items over all segments (load balance of the
+  // persistent profile kernel), at least 1024, never more split items than partial rows.
+  {
+    unsigned long long tot = 0;
+    for (int64_t i = a; i < b; ++i) {
+      int64_t s = i % nseg;
+      tot += (unsigned long long)(segr[nseg + s] - segr[s]);
+    }
+    part[threadIdx.x] = tot;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long all = 0;
+      for (int i = 0; i < (int)blockDim.x; ++i) all += part[i];
+      long long L = item_lines_max;
+      if (target_items > 0 && item_lines_max < (1 << 30)) {
+        long long t = (long long)((all + target_items - 1) / target_items);
+        long long m = (long long)((all + max_partial - 1) / (max_partial > 0 ? max_partial : 1));
+        t = t > 512 ? t : 512;
+        t = t > m ? t : m;
+        t = (t + 255) / 256 * 256;
+        L = t < item_lines_max ? t : item_lines_max;
+      }
+      item_lines_sh = (int)L;
+    }
+    __syncthreads();
+  }
+  const int item_lines = item_lines_sh;
   auto count = [&](int64_t gi) -> int64_t {
     int64_t s = gi % nseg;
     int64_t nl = (int64_t)segr[nseg + s] - segr[s];
@@ -635,8 +835,10 @@ __global__ void k_items(const int32_t* __restrict__ segr, int64_t nseg, int n_c,
 }
 
 void launch_items(const int32_t* segr, int64_t nseg, int n_c, int item_lines, int32_t* seg_items, Item* items,
-                  unsigned long long* counters, int64_t max_items, cudaStream_t s) {
-  k_items<<<1, 1024, 0, s>>>(segr, nseg, n_c, item_lines, seg_items, items, counters, max_items);
+                  unsigned long long* counters, int64_t max_items, int64_t target_items, int64_t max_partial,
+                  cudaStream_t s) {
+  k_items<<<1, 1024, 0, s>>>(segr, nseg, n_c, item_lines, seg_items, items, counters, max_items, target_items,
+                             max_partial);
   note_launches(1);
 }
 

@@ -165,7 +165,36 @@ __device__ __noinline__ void w4_full(float x, float y, cplx* w, cplx* dw) {
   *dw = {dwdt.i, -dwdt.r};
 }
 
-// Real part of W4 only (forward).
+// Real part of W4 in regions II-IV (|x| + y < 15), forward only.  Kept out of line so the
+// branch-free far-wing loop of the profile kernel stays small in registers.
+__device__ __noinline__ float w4_core_re(float x, float y) {
+  const float ax = fabsf(x), s = ax + y;
+  const cplx t = {y, -x};
+  const cplx u = cmul(t, t);
+  if (s >= 5.5f) {
+    // w = t (1.410474 + 0.5641896 u) / (0.75 + u (3 + u))
+    cplx N = {1.410474f + 0.5641896f * u.r, 0.5641896f * u.i};
+    cplx D = cadd(cmul(u, cadd(u, 3.f)), 0.75f);
+    return cdiv(cmul(t, N), D).r;
+  }
+  if (y >= 0.195f * ax - 0.176f) {
+    cplx P = cadd(cmul(t, cadd(cmul(t, cadd(cmul(t, cadd(cmul(t, {0.5642236f, 0.f}), 3.778987f)), 11.96482f)), 20.20933f)),
+                  16.4955f);
+    cplx Q = cadd(cmul(t, cadd(cmul(t, cadd(cmul(t, cadd(cmul(t, cadd(t, 6.699398f)), 21.69274f)), 39.27121f)),
+                               38.82363f)),
+                  16.4955f);
+    return cdiv(P, Q).r;
+  }
+  cplx P = csub_from(36183.31f, cmul(u, csub_from(3321.9905f, cmul(u, csub_from(1540.787f, cmul(u, csub_from(219.0313f,
+               cmul(u, csub_from(35.76683f, cmul(u, csub_from(1.320522f, {0.56419f * u.r, 0.56419f * u.i})))))))))));
+  cplx Q = csub_from(32066.6f, cmul(u, csub_from(24322.84f, cmul(u, csub_from(9022.228f, cmul(u, csub_from(2186.181f,
+               cmul(u, csub_from(364.2191f, cmul(u, csub_from(61.57037f, cmul(u, csub_from(1.841439f, u)))))))))))));
+  const float eu = expf(u.r);
+  const float cs = cosf(u.i);
+  return eu * cs - cmul(t, cdiv(P, Q)).r;
+}
+
+// Real part of W4 in every region (used by the general path).
 __device__ __forceinline__ float w4_re(float x, float y) {
   const float ax = fabsf(x), s = ax + y;
   if (s >= 15.f) {
@@ -173,17 +202,26 @@ __device__ __forceinline__ float w4_re(float x, float y) {
     float den = fmaf(x2, x2 + (2.f * y2 - 1.f), A * A);
     return kInvSqrtPi * y * (A + x2) * frcp(den);
   }
-  cplx w, dw;
-  w4_full(x, y, &w, &dw);
-  return w.r;
+  return w4_core_re(x, y);
 }
 
 // ------------------------------------------------------------------ forward kernel
+// Warp w of a CTA owns the points [512 w, 512 w + 512) of the CTA's segment; lane l holds
+// the points 256 w + l + 32 k, k < kPts.  For every staged line one thread precomputes two
+// 8-bit masks over the warps: `fast` (the warp's points all lie inside the cut-off window and
+// in W4 region I, so the branch-free far-wing formula applies with no mask) and `touch` (the
+// window meets the warp's points).  A warp tests its bits once per line.
+constexpr int kWarpPts = 32 * kPts;          // 512 points per warp
+constexpr int kWarps = kThreadsV / 32;
+
 struct __align__(16) LineC {
-  float pf, step, nfs, B1;     // fast: centre offset, step, -f*step, 2y^2-1 (Voigt) / gamma^2 (Lorentz)
-  float A2, K, KA, y;          // fast: A^2, K, K*A, y
-  int lo, hi, flags;           // window relative to the segment; bit0 skip, bit1 fast
-  float Kc;                    // amplitude for the general path
+  float pf, step, nfs, B1;     // centre offset (grid steps, exact integer part), step, -f*step, 2y^2-1 | gamma^2
+  float A2, K, KA, y;          // region-I constants (Voigt), Lorentz/Gauss amplitude in K
+  int lo, hi;                  // window relative to the segment (grid points, clamped)
+  int masks;                   // bits 0-7 fast warps, 8-15 far warps with a window edge, 16-23 warps near the core
+  float Kc;                    // amplitude of the general path
+  float reach, cen;            // half-width of the non-region-I zone and the centre (grid steps)
+  float pad0, pad1;
 };
 
 constexpr int kStageBytes = kStageLines * (16 + 8 + 4);
@@ -193,65 +231,81 @@ constexpr int kStageBytes = kStageLines * (16 + 8 + 4);
 constexpr float kAlphaMin = 8.4e-8f;
 // Smallest Lorentz HWHM used (cm^-1): gamma^2 stays a normal FP32 number.
 constexpr float kGammaMin = 1e-15f;
-constexpr int FLAG_SKIP = 1, FLAG_FAST = 2;
 
 template <int KIND>
 __device__ __forceinline__ void line_constants(const int4 p4, const float2 pr, const float is, const CondDev& cd,
-                                               int64_t i0, float dnu_f, double nu_min, double dnu, LineC& c) {
+                                               int64_t i0, float dnu_f, double nu_min, double dnu, bool valid,
+                                               LineC& c) {
   const int ic = p4.x;
   const float f = __int_as_float(p4.y);
   c.pf = (float)((int64_t)ic - i0);
-  int64_t lo = (int64_t)p4.z - i0, hi = (int64_t)p4.w - i0;
+  const int64_t lo = (int64_t)p4.z - i0, hi = (int64_t)p4.w - i0;
   c.lo = (int)(lo < 0 ? 0 : lo);
   c.hi = (int)(hi > kSeg - 1 ? kSeg - 1 : hi);
-  c.flags = is == 0.f ? FLAG_SKIP : 0;
-  const bool full = lo <= 0 && hi >= kSeg - 1;
-  // distance (grid steps) from the line centre to the nearest point of the segment
-  const float cen = c.pf + f;
-  const float dmin = fmaxf(0.f, fmaxf(cen - (float)(kSeg - 1), -cen));
+  const float cen = c.pf + f;  // line centre in grid steps from the segment start
+  float reach = 0.f;           // half-width (grid steps) of the zone needing the general path
   if (KIND == PXC_LORENTZ) {
-    float g = fmaxf(pr.x * exp2f(pr.y * cd.log2_tratio) * cd.P_f, kGammaMin);
+    const float g = fmaxf(pr.x * exp2f(pr.y * cd.log2_tratio) * cd.P_f, kGammaMin);
     c.step = dnu_f;
     c.nfs = -f * dnu_f;
     c.B1 = g * g;
     c.Kc = is * g * kInvPi;
     c.K = c.Kc;
     c.A2 = 0.f; c.KA = 0.f; c.y = g;
-    if (full) c.flags |= FLAG_FAST;
   } else {
-    float nu = (float)(nu_min + ((double)ic + (double)f) * dnu);
-    float alpha = fmaxf(KIND == PXC_GAUSS_HWHM ? cd.hwhm : cd.alpha_coef * nu, kAlphaMin);
-    float cc = kSqrtLn2 / alpha;             // 1 / (s sqrt 2)
+    const float nu = (float)(nu_min + ((double)ic + (double)f) * dnu);
+    const float alpha = fmaxf(KIND == PXC_GAUSS_HWHM ? cd.hwhm : cd.alpha_coef * nu, kAlphaMin);
+    const float cc = kSqrtLn2 / alpha;       // 1 / (s sqrt 2)
     if (KIND == PXC_VOIGT) {
-      float g = pr.x * exp2f(pr.y * cd.log2_tratio) * cd.P_f;
-      float y = g * cc;
+      const float g = pr.x * exp2f(pr.y * cd.log2_tratio) * cd.P_f;
+      const float y = g * cc;
       c.y = y;
       c.step = dnu_f * cc;
       c.nfs = -f * c.step;
-      float A = 0.5f + y * y;
+      const float A = 0.5f + y * y;
       c.B1 = 2.f * y * y - 1.f;
       c.A2 = A * A;
       c.Kc = is * cc * kInvSqrtPi;
       c.K = c.Kc * y * kInvSqrtPi;
       c.KA = c.K * A;
-      if (full && dmin * c.step + y >= 15.f) c.flags |= FLAG_FAST;
+      reach = fmaxf(15.f - y, 0.f) / c.step;
     } else {
-      // Gaussian: exp(-X^2) = 2^(-(X sqrt(log2 e))^2); scale x by sqrt(log2 e)
+      // exp(-X^2) = 2^(-(X sqrt(log2 e))^2); x is scaled by sqrt(log2 e)
       const float sl2e = 1.2011224087864498f;
       c.step = dnu_f * cc * sl2e;
       c.nfs = -f * c.step;
       c.Kc = is * cc * kInvSqrtPi;
       c.K = c.Kc;
       c.y = 0.f; c.B1 = 0.f; c.A2 = 0.f; c.KA = 0.f;
-      // provably-zero trim: 2^(-t) with t > 159 is below the FP32 range of any product here
-      float reach = 12.7f / c.step;          // |X'| <= 12.7 <=> X^2 <= 111.8
-      float elo = ceilf(cen - reach), ehi = floorf(cen + reach);
+      // provably-zero trim: 2^(-t) for t > 159 is below the FP32 range of every product here
+      const float r = 12.7f / c.step;        // |X'| <= 12.7 <=> X^2 <= 111.8
+      const float elo = ceilf(cen - r), ehi = floorf(cen + r);
       if (elo > (float)c.lo) c.lo = (int)fminf(elo, (float)kSeg);
       if (ehi < (float)c.hi) c.hi = (int)fmaxf(ehi, -1.f);
-      if (c.lo == 0 && c.hi == kSeg - 1 && full) c.flags |= FLAG_FAST;
-      if (c.lo > c.hi) c.flags |= FLAG_SKIP;
     }
   }
+  // Per warp: fast (inside the window and in region I), far-but-partial (region I, window edge
+  // among the warp's points: same formula with a lane mask), slow (the line core is near).
+  int fast = 0, fmask = 0, slow = 0;
+  if (valid && is != 0.f && c.lo <= c.hi) {
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      const int a = w * kWarpPts, b = a + kWarpPts - 1;
+      if (c.hi < a || c.lo > b) continue;
+      const bool full = c.lo <= a && c.hi >= b;
+      bool far = true;
+      if (KIND == PXC_VOIGT) {
+        const float dmin = fmaxf(0.f, fmaxf(cen - (float)b, (float)a - cen));
+        far = dmin > reach;
+      }
+      if (!far) slow |= 1 << w;
+      else if (full) fast |= 1 << w;
+      else fmask |= 1 << w;
+    }
+  }
+  c.masks = fast | (fmask << 8) | (slow << 16);
+  c.reach = reach;
+  c.cen = cen;
 }
 
 template <int KIND>
@@ -261,19 +315,140 @@ __device__ __forceinline__ float eval_general(float x, const LineC& c) {
   return c.K * fex2(-(x * x));
 }
 
+// Branch-free evaluation of one line at the lane's kPts points (fast warps).
 template <int KIND>
-__global__ void __launch_bounds__(kThreadsV, 2) k_profile(const ProfP p) {
-  __shared__ __align__(128) unsigned char raw[kStages][kStageBytes];
-  __shared__ LineC lc[kStageLines];
+__device__ __forceinline__ void eval_fast(const LineC& c, float lane_f, float* acc) {
+  if (KIND == PXC_VOIGT) {
+    // far wing, W4 region I: Re w = y (A + x^2) / (sqrt(pi) ((A - x^2)^2 + 4 x^2 y^2)), A = 1/2 + y^2;
+    // no point of this warp is near the centre, so x = x0 + 32 k step keeps full relative accuracy
+    const float4 f0 = *reinterpret_cast<const float4*>(&c.pf);   // pf, step, nfs, B1
+    const float4 f1 = *reinterpret_cast<const float4*>(&c.A2);   // A2, K, KA, y
+    const float x0 = fmaf(lane_f - f0.x, f0.y, f0.z);
+    const float s32 = 32.f * f0.y;
+#pragma unroll
+    for (int k = 0; k < kPts; ++k) {
+      const float x = fmaf((float)k, s32, x0);
+      const float x2 = x * x;
+      const float den = fmaf(x2, x2 + f0.w, f1.x);
+      acc[k] = fmaf(fmaf(x2, f1.y, f1.z), frcp(den), acc[k]);
+    }
+  } else {
+    // the line centre may lie among these points: x from the exact integer offset
+    const float4 f0 = *reinterpret_cast<const float4*>(&c.pf);
+    const float K = c.K;
+#pragma unroll
+    for (int k = 0; k < kPts; ++k) {
+      const float x = fmaf(lane_f + (float)(32 * k) - f0.x, f0.y, f0.z);
+      if (KIND == PXC_LORENTZ) acc[k] = fmaf(K, frcp(fmaf(x, x, f0.w)), acc[k]);
+      else acc[k] = fmaf(K, fex2(-(x * x)), acc[k]);
+    }
+  }
+}
+
+// Two lines at once (more independent work per point, half the loop overhead).
+template <int KIND>
+__device__ __forceinline__ void eval_fast2(const LineC& c, const LineC& d, float lane_f, float* acc) {
+  if (KIND == PXC_VOIGT) {
+    const float4 a0 = *reinterpret_cast<const float4*>(&c.pf), a1 = *reinterpret_cast<const float4*>(&c.A2);
+    const float4 b0 = *reinterpret_cast<const float4*>(&d.pf), b1 = *reinterpret_cast<const float4*>(&d.A2);
+    const float xa = fmaf(lane_f - a0.x, a0.y, a0.z), sa = 32.f * a0.y;
+    const float xb = fmaf(lane_f - b0.x, b0.y, b0.z), sb = 32.f * b0.y;
+#pragma unroll
+    for (int k = 0; k < kPts; ++k) {
+      const float x = fmaf((float)k, sa, xa), y = fmaf((float)k, sb, xb);
+      const float x2 = x * x, y2 = y * y;
+      const float ra = frcp(fmaf(x2, x2 + a0.w, a1.x)), rb = frcp(fmaf(y2, y2 + b0.w, b1.x));
+      acc[k] = fmaf(fmaf(x2, a1.y, a1.z), ra, fmaf(fmaf(y2, b1.y, b1.z), rb, acc[k]));
+    }
+  } else {
+    eval_fast<KIND>(c, lane_f, acc);
+    eval_fast<KIND>(d, lane_f, acc);
+  }
+}
+
+// Far-wing formula with a lane mask (the window ends among this warp's points).
+template <int KIND>
+__device__ __forceinline__ void eval_fastmask(const LineC& c, int wbase, int lane, float* acc) {
+  const unsigned span = (unsigned)(c.hi - c.lo);
+  const int rel0 = wbase + lane - c.lo;
+  if (KIND == PXC_VOIGT) {
+    const float x0 = fmaf((float)(wbase + lane) - c.pf, c.step, c.nfs);
+    const float s32 = 32.f * c.step;
+#pragma unroll
+    for (int k = 0; k < kPts; ++k) {
+      const float x = fmaf((float)k, s32, x0);
+      const float x2 = x * x;
+      const float den = fmaf(x2, x2 + c.B1, c.A2);
+      const float v = fmaf(x2, c.K, c.KA) * frcp(den);
+      acc[k] += (unsigned)(rel0 + 32 * k) <= span ? v : 0.f;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kPts; ++k) {
+      const float x = fmaf((float)(wbase + lane + 32 * k) - c.pf, c.step, c.nfs);
+      const float v = KIND == PXC_LORENTZ ? c.K * frcp(fmaf(x, x, c.B1)) : c.K * fex2(-(x * x));
+      acc[k] += (unsigned)(rel0 + 32 * k) <= span ? v : 0.f;
+    }
+  }
+}
+
+// Warps near the line core (Voigt): blocks of 32 points far from the centre keep the
+// region-I formula; elsewhere each point takes its W4 region.  Region II
+// (5.5 <= |x|+y < 15) is evaluated as the real rational Re w = y N(X) / D(X) in X = x^2
+// (N cubic, D monic quartic, coefficients from Y = y^2 once per line and warp; Humlicek's
+// constants satisfy a = 2.5 b, which gives the factored forms below); only |x|+y < 5.5
+// needs the complex regions III/IV.
+template <int KIND>
+__device__ __forceinline__ void eval_slow(const LineC& c, int wbase, int lane, float* acc) {
+  const unsigned span = (unsigned)(c.hi - c.lo);
+  const float bq = 0.5641896f;
+  const float Y = c.y * c.y;
+  const float n3 = bq, n2 = bq * (3.f * Y - 4.5f), n1 = bq * ((3.f * Y + 1.f) * Y + 5.25f);
+  const float n0 = 0.125f * bq * (2.f * Y + 5.f) * ((4.f * Y + 12.f) * Y + 3.f);
+  const float d3 = 4.f * Y - 6.f, d2 = (6.f * Y - 6.f) * Y + 10.5f, d1 = ((4.f * Y + 6.f) * Y + 9.f) * Y - 4.5f;
+  const float d0 = (((Y + 6.f) * Y + 10.5f) * Y + 4.5f) * Y + 0.5625f;
+  const float Ky = c.Kc * c.y;
+#pragma unroll
+  for (int k = 0; k < kPts; ++k) {
+    const int b0 = wbase + 32 * k;
+    if (b0 > c.hi || b0 + 31 < c.lo) continue;
+    const int li = b0 + lane;
+    const float x = fmaf((float)li - c.pf, c.step, c.nfs);
+    const bool in = (unsigned)(li - c.lo) <= span;
+    const float dmin = fmaxf(0.f, fmaxf(c.cen - (float)(b0 + 31), (float)b0 - c.cen));
+    float v;
+    const float x2 = x * x;
+    if (dmin > c.reach || fabsf(x) + c.y >= 15.f) {
+      v = fmaf(x2, c.K, c.KA) * frcp(fmaf(x2, x2 + c.B1, c.A2));
+    } else if (fabsf(x) + c.y >= 5.5f) {
+      const float N = fmaf(fmaf(fmaf(n3, x2, n2), x2, n1), x2, n0);
+      const float D = fmaf(fmaf(fmaf(x2 + d3, x2, d2), x2, d1), x2, d0);
+      v = Ky * N * frcp(D);
+    } else {
+      v = c.Kc * w4_core_re(x, c.y);
+    }
+    acc[k] += in ? v : 0.f;
+  }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kThreadsV, 4) k_profile(const ProfP p) {
+  extern __shared__ __align__(128) unsigned char dyn_smem[];
+  unsigned char (*raw)[kStageBytes] = reinterpret_cast<unsigned char (*)[kStageBytes]>(dyn_smem);
+  LineC* lc = reinterpret_cast<LineC*>(dyn_smem + kStages * kStageBytes);
+  // per warp, the staged lines it evaluates, in line order: fast ones, then the others
+  uint16_t* lists = reinterpret_cast<uint16_t*>(dyn_smem + kStages * kStageBytes + kStageLines * sizeof(LineC));
   __shared__ __align__(8) uint64_t bar[kStages];
   __shared__ Item item_sh;
-  __shared__ int abort_sh;
 
   const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int wbase = warp * kWarpPts;
+  const float lane_f = (float)(wbase + lane);
+  const int wbit = 1 << warp, mbit = 1 << (warp + 8), sbit = 1 << (warp + 16);
   if (tid == 0) {
     for (int b = 0; b < kStages; ++b) mbar_init(&bar[b], 1);
     fence_mbar_init();
-    abort_sh = 0;
   }
   __syncthreads();
   unsigned phase = 0;  // bit b: parity to wait for on buffer b
@@ -294,9 +469,9 @@ __global__ void __launch_bounds__(kThreadsV, 2) k_profile(const ProfP p) {
     const int j0 = item.begin & ~3;
     const int nst = item.end > item.begin ? (item.end - j0 + kStageLines - 1) / kStageLines : 0;
 
-    float sum[kPts], cmp[kPts];
+    float sum[kPts];
 #pragma unroll
-    for (int q = 0; q < kPts; ++q) { sum[q] = 0.f; cmp[q] = 0.f; }
+    for (int k = 0; k < kPts; ++k) sum[k] = 0.f;
 
     auto issue = [&](int st) {
       const int b = st % kStages;
@@ -314,18 +489,19 @@ __global__ void __launch_bounds__(kThreadsV, 2) k_profile(const ProfP p) {
     bool aborted = false;
     for (int st = 0; st < nst; ++st) {
       const int b = st % kStages;
-      bool ok = mbar_wait_bounded(&bar[b], (phase >> b) & 1u, p.spin_limit);
+      const bool ok = mbar_wait_bounded(&bar[b], (phase >> b) & 1u, p.spin_limit);
       phase ^= 1u << b;
       if (__syncthreads_or(!ok)) { aborted = true; break; }
-      {
-        const int64_t J = (int64_t)j0 + (int64_t)st * kStageLines + tid;
-        const int4 p4 = reinterpret_cast<const int4*>(raw[b])[tid];
-        const float2 pr = reinterpret_cast<const float2*>(raw[b] + kStageLines * 16)[tid];
-        const float is = reinterpret_cast<const float*>(raw[b] + kStageLines * 24)[tid];
+#pragma unroll
+      for (int r = 0; r < kStageLines / kThreadsV; ++r) {
+        const int j = tid + r * kThreadsV;
+        const int64_t J = (int64_t)j0 + (int64_t)st * kStageLines + j;
+        const int4 p4 = reinterpret_cast<const int4*>(raw[b])[j];
+        const float2 pr = reinterpret_cast<const float2*>(raw[b] + kStageLines * 16)[j];
+        const float is = reinterpret_cast<const float*>(raw[b] + kStageLines * 24)[j];
         LineC c;
-        line_constants<KIND>(p4, pr, is, cd, i0, dnu_f, p.nu_min, p.dnu, c);
-        if (J < item.begin || J >= item.end) c.flags = FLAG_SKIP;
-        lc[tid] = c;
+        line_constants<KIND>(p4, pr, is, cd, i0, dnu_f, p.nu_min, p.dnu, J >= item.begin && J < item.end, c);
+        lc[j] = c;
       }
       __syncthreads();
       if (tid == 0 && st + kStages < nst) {
@@ -334,103 +510,90 @@ __global__ void __launch_bounds__(kThreadsV, 2) k_profile(const ProfP p) {
       }
       float acc[kPts];
 #pragma unroll
-      for (int q = 0; q < kPts; ++q) acc[q] = 0.f;
-      const float tf = (float)tid;
-      for (int l = 0; l < kStageLines; ++l) {
-        const LineC& c = lc[l];
-        const int flags = c.flags;
-        if (flags & FLAG_SKIP) continue;
-        if (flags & FLAG_FAST) {
-          const float x0 = fmaf(tf - c.pf, c.step, c.nfs);
-          const float s256 = 256.f * c.step;
-          if (KIND == PXC_VOIGT) {
-#pragma unroll
-            for (int q = 0; q < kPts; ++q) {
-              const float x = fmaf((float)q, s256, x0);
-              const float x2 = x * x;
-              const float den = fmaf(x2, x2 + c.B1, c.A2);
-              acc[q] = fmaf(fmaf(x2, c.K, c.KA), frcp(den), acc[q]);
-            }
-          } else if (KIND == PXC_LORENTZ) {
-#pragma unroll
-            for (int q = 0; q < kPts; ++q) {
-              const float x = fmaf((float)q, s256, x0);
-              acc[q] = fmaf(c.K, frcp(fmaf(x, x, c.B1)), acc[q]);
-            }
-          } else {
-#pragma unroll
-            for (int q = 0; q < kPts; ++q) {
-              const float x = fmaf((float)q, s256, x0);
-              acc[q] = fmaf(c.K, fex2(-(x * x)), acc[q]);
-            }
-          }
-        } else {
-#pragma unroll
-          for (int q = 0; q < kPts; ++q) {
-            const int li = tid + 256 * q;
-            if (li >= c.lo && li <= c.hi) {
-              const float x = fmaf((float)li - c.pf, c.step, c.nfs);
-              acc[q] += eval_general<KIND>(x, c);
-            }
-          }
-        }
+      for (int k = 0; k < kPts; ++k) acc[k] = 0.f;
+      // this warp's lines of the stage, compacted in line order
+      uint16_t* fl = lists + warp * 2 * kStageLines;
+      uint16_t* ol = fl + kStageLines;
+      int nf = 0, no = 0;
+      const unsigned lt = (1u << lane) - 1u;
+#pragma unroll 2
+      for (int c0 = 0; c0 < kStageLines; c0 += 32) {
+        const int m = lc[c0 + lane].masks;
+        const unsigned bf = __ballot_sync(0xffffffffu, (m & wbit) != 0);
+        const unsigned bo = __ballot_sync(0xffffffffu, (m & (mbit | sbit)) != 0);
+        if (m & wbit) fl[nf + __popc(bf & lt)] = (uint16_t)(c0 + lane);
+        if (m & (mbit | sbit)) ol[no + __popc(bo & lt)] = (uint16_t)(c0 + lane);
+        nf += __popc(bf);
+        no += __popc(bo);
       }
-      // compensated fold of the stage sums (Knuth two-sum)
-#pragma unroll
-      for (int q = 0; q < kPts; ++q) {
-        float s = sum[q] + acc[q];
-        float bp = s - sum[q];
-        float err = (sum[q] - (s - bp)) + (acc[q] - bp);
-        sum[q] = s;
-        cmp[q] += err;
+      __syncwarp();
+      int i = 0;
+      for (; i + 1 < nf; i += 2) eval_fast2<KIND>(lc[fl[i]], lc[fl[i + 1]], lane_f, acc);
+      if (i < nf) eval_fast<KIND>(lc[fl[i]], lane_f, acc);
+      for (int j = 0; j < no; ++j) {
+        const LineC& c = lc[ol[j]];
+        if (c.masks & mbit) eval_fastmask<KIND>(c, wbase, lane, acc);
+        else eval_slow<KIND>(c, wbase, lane, acc);
       }
+#pragma unroll
+      for (int k = 0; k < kPts; ++k) sum[k] += acc[k];
       __syncthreads();
     }
     if (aborted) {
-      if (tid == 0) {
-        atomicOr(p.err, ERRB_TIMEOUT);
-        abort_sh = 1;
-      }
+      if (tid == 0) atomicOr(p.err, ERRB_TIMEOUT);
       // let copies already in flight land before the CTA leaves (bounded again)
       for (int b = 0; b < kStages; ++b) mbar_wait_bounded(&bar[b], (phase >> b) & 1u, p.spin_limit);
       break;
     }
-    // write the segment
 #pragma unroll
-    for (int q = 0; q < kPts; ++q) {
-      const int li = tid + 256 * q;
+    for (int k = 0; k < kPts; ++k) {
+      const int li = wbase + lane + 32 * k;
       const int64_t i = i0 + li;
-      const float v = sum[q] + cmp[q];
       if (item.slot < 0) {
         if (i < p.n_grid) {
           float* o = p.sigma + (int64_t)item.cond * p.n_grid + i;
-          if (p.accumulate) { if (nst) *o += v; } else *o = v;
+          if (p.accumulate) { if (nst) *o += sum[k]; } else *o = sum[k];
         }
       } else {
-        p.partial[(int64_t)item.slot * kSeg + li] = v;
+        p.partial[(int64_t)item.slot * kSeg + li] = sum[k];
       }
     }
     __syncthreads();
   }
 }
 
+constexpr size_t kProfileSmem = (size_t)kStages * kStageBytes + (size_t)kStageLines * sizeof(LineC) +
+                               (size_t)kWarps * 2 * kStageLines * sizeof(uint16_t);
+
+template <int KIND>
+static int occupancy_of() {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_profile<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kProfileSmem);
+    attr = true;
+  }
+  int n = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_profile<KIND>, kThreadsV, kProfileSmem);
+  return n;
+}
+
 int profile_occupancy(int kind) {
   int n = 0;
   switch (kind) {
-    case PXC_GAUSS_DOPPLER: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_profile<PXC_GAUSS_DOPPLER>, kThreadsV, 0); break;
-    case PXC_GAUSS_HWHM: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_profile<PXC_GAUSS_HWHM>, kThreadsV, 0); break;
-    case PXC_LORENTZ: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_profile<PXC_LORENTZ>, kThreadsV, 0); break;
-    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_profile<PXC_VOIGT>, kThreadsV, 0); break;
+    case PXC_GAUSS_DOPPLER: n = occupancy_of<PXC_GAUSS_DOPPLER>(); break;
+    case PXC_GAUSS_HWHM: n = occupancy_of<PXC_GAUSS_HWHM>(); break;
+    case PXC_LORENTZ: n = occupancy_of<PXC_LORENTZ>(); break;
+    default: n = occupancy_of<PXC_VOIGT>(); break;
   }
   return n > 0 ? n : 1;
 }
 
 void launch_profile(const ProfP& p, int grid_ctas, cudaStream_t s) {
   switch (p.kind) {
-    case PXC_GAUSS_DOPPLER: k_profile<PXC_GAUSS_DOPPLER><<<grid_ctas, kThreadsV, 0, s>>>(p); break;
-    case PXC_GAUSS_HWHM: k_profile<PXC_GAUSS_HWHM><<<grid_ctas, kThreadsV, 0, s>>>(p); break;
-    case PXC_LORENTZ: k_profile<PXC_LORENTZ><<<grid_ctas, kThreadsV, 0, s>>>(p); break;
-    default: k_profile<PXC_VOIGT><<<grid_ctas, kThreadsV, 0, s>>>(p); break;
+    case PXC_GAUSS_DOPPLER: k_profile<PXC_GAUSS_DOPPLER><<<grid_ctas, kThreadsV, kProfileSmem, s>>>(p); break;
+    case PXC_GAUSS_HWHM: k_profile<PXC_GAUSS_HWHM><<<grid_ctas, kThreadsV, kProfileSmem, s>>>(p); break;
+    case PXC_LORENTZ: k_profile<PXC_LORENTZ><<<grid_ctas, kThreadsV, kProfileSmem, s>>>(p); break;
+    default: k_profile<PXC_VOIGT><<<grid_ctas, kThreadsV, kProfileSmem, s>>>(p); break;
   }
   note_launches(1);
 }

@@ -37,7 +37,7 @@ constexpr int kWinCap = 16384;  // largest cut-off window (points) the item tabl
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t err, counters, qpart, qres, slots, cond, srec, key, Iv, bcount, skey0, skey1, sidx0, sidx1, rcount, pos,
+  size_t err, counters, qpart, qres, slots, cond, srec, sfast, key, Iv, bcount, skey0, skey1, sidx0, sidx1, rcount, pos,
       par, Is, su, sl, sA, sI, segr, seg_items, items, partial, kexp, maxbits, params, total;
   int64_t max_seg, max_items, max_partial, max_slots, nblk_I, nblk_sort, max_cond, is_stride;
 };
@@ -63,6 +63,7 @@ Layout make_layout(const pxc_capacity& c) {
   L.slots = take((size_t)L.max_cond * sizeof(SlotP));
   L.cond = take((size_t)L.max_cond * sizeof(CondDev));
   L.srec = take((size_t)std::max<int64_t>(c.max_states, 1) * 16);
+  L.sfast = take((size_t)std::max<int64_t>(c.max_states, 1) * sizeof(StateFast));
   L.key = take((size_t)ml * 8);
   L.Iv = take((size_t)ml * 8);
   L.bcount = take((size_t)(L.nblk_I + 1) * 4);
@@ -253,10 +254,19 @@ void run_boltzmann(pxc_workspace* ws, const pxc_states* st, const pxc_condition&
   SlotP sp = make_slot(c);
   SlotP* dslot = at<SlotP>(ws, x->L.slots) + slot;
   upload(ws, dslot, &sp, sizeof sp, s);
-  launch_boltzmann(st, dslot, 1, at<double2>(ws, x->L.srec), 0, at<double>(ws, x->L.qpart),
-                   at<double>(ws, x->L.qres) + 4 * slot, ws->err, s);
+  launch_boltzmann(st, dslot, 1, at<double2>(ws, x->L.srec), 0, at<StateFast>(ws, x->L.sfast),
+                   at<double>(ws, x->L.qpart), at<double>(ws, x->L.qres) + 4 * slot, ws->err, s);
   ws->cache_valid = allow_cache ? 1 : 0;
   ws->cache_E = st->E; ws->cache_n = st->n; ws->cache_T = c.T; ws->cache_Tv = c.T_vib;
+}
+
+BoundP make_bound(const pxc_condition& c, double threshold) {
+  BoundP bp{};
+  bp.log2_thr = threshold > 0.0 ? (float)(std::log2(threshold) - 1e-3) : -INFINITY;
+  bp.log2_invQ = 0.f;
+  bp.lte = c.T_vib > 0.0 ? 0 : 1;
+  bp.c2_T = (float)(kH * kC / kKB / c.T);
+  return bp;
 }
 
 // Lines -> kept, sorted, prepared (plain single-condition path).  with_gather fills su/sl/sA.
@@ -270,14 +280,15 @@ pxc_status front_plain(pxc_workspace* ws, const pxc_states* st, const pxc_transi
   cudaMemsetAsync(at<unsigned long long>(ws, L.maxbits), 0, 8, s);
   const int64_t nblk = (tr->n + kLinesPerBlockI - 1) / kLinesPerBlockI;
   tmark(ws, 0, true, s);
-  launch_lines(tr, st->g, st->n, at<double2>(ws, L.srec), at<double>(ws, L.qres), gp, 1, threshold, 1,
-               at<uint64_t>(ws, L.key), at<double>(ws, L.Iv), nullptr, at<uint32_t>(ws, L.bcount), nblk,
-               at<unsigned long long>(ws, L.maxbits), ws->err, s);
+  BoundP bp = make_bound(c, threshold);
+  launch_lines_compact(tr, st->n, at<StateFast>(ws, L.sfast), at<double2>(ws, L.srec), at<double>(ws, L.qres), gp,
+                       threshold, bp, 1, at<uint64_t>(ws, L.key), at<uint32_t>(ws, L.sidx1), at<double>(ws, L.Iv),
+                       at<uint32_t>(ws, L.bcount), nblk, at<unsigned long long>(ws, L.maxbits), ws->err, s);
   tmark(ws, 0, false, s);
   tmark(ws, 1, true, s);
   if (nblk) launch_scan_counts(at<uint32_t>(ws, L.bcount), nblk, cnt + CNT_KEPT, s);
-  launch_compact(at<uint64_t>(ws, L.key), tr->n, at<uint32_t>(ws, L.bcount), at<uint64_t>(ws, L.skey0),
-                 at<uint32_t>(ws, L.sidx0), s);
+  launch_compact_staged(at<uint64_t>(ws, L.key), at<uint32_t>(ws, L.sidx1), at<uint32_t>(ws, L.bcount), nblk,
+                        at<uint64_t>(ws, L.skey0), at<uint32_t>(ws, L.sidx0), s);
   uint64_t* keys[2] = {at<uint64_t>(ws, L.skey0), at<uint64_t>(ws, L.skey1)};
   uint32_t* idxs[2] = {at<uint32_t>(ws, L.sidx0), at<uint32_t>(ws, L.sidx1)};
   launch_radix_sort(keys, idxs, cnt + CNT_KEPT, tr->n, at<uint32_t>(ws, L.rcount), s);
@@ -415,7 +426,7 @@ pxc_status pxc_partition_function(pxc_workspace* ws, const pxc_states* st, const
   SlotP* dslot = at<SlotP>(ws, x->L.slots);
   if ((r = upload(ws, dslot, sp.data(), sizeof(SlotP) * n_c, s))) return r;
   double* qres = at<double>(ws, x->L.qres);
-  launch_boltzmann(st, dslot, n_c, nullptr, 0, at<double>(ws, x->L.qpart), qres, ws->err, s);
+  launch_boltzmann(st, dslot, n_c, nullptr, 0, nullptr, at<double>(ws, x->L.qpart), qres, ws->err, s);
   for (int i = 0; i < n_c; ++i) {
     cudaMemcpyAsync(Q_out + i, qres + 4 * i, 8, cudaMemcpyDeviceToDevice, s);
     if (dQ_out) cudaMemcpyAsync(dQ_out + 2 * i, qres + 4 * i + 1, 16, cudaMemcpyDeviceToDevice, s);
@@ -513,10 +524,12 @@ pxc_status pxc_cross_section(pxc_workspace* ws, const pxc_states* st, const pxc_
     // The geometry pass reads E through the state table, so fill it (first slot) first.
     run_boltzmann(ws, st, slots[0], 0, s, false);
     const int64_t nblk = (tr->n + kLinesPerBlockI - 1) / kLinesPerBlockI;
-    launch_lines(tr, st->g, st->n, at<double2>(ws, L.srec), at<double>(ws, L.qres), gp, 1, 0.0, 0,
-                 at<uint64_t>(ws, L.key), nullptr, nullptr, at<uint32_t>(ws, L.bcount), nblk, nullptr, ws->err, s);
+    BoundP bp = make_bound(c[0], 0.0);
+    launch_lines_compact(tr, st->n, at<StateFast>(ws, L.sfast), at<double2>(ws, L.srec), at<double>(ws, L.qres), gp,
+                         0.0, bp, 0, at<uint64_t>(ws, L.key), idxs[1], nullptr, at<uint32_t>(ws, L.bcount), nblk,
+                         nullptr, ws->err, s);
     if (nblk) launch_scan_counts(at<uint32_t>(ws, L.bcount), nblk, cnt + CNT_KEPT, s);
-    launch_compact(at<uint64_t>(ws, L.key), tr->n, at<uint32_t>(ws, L.bcount), keys[0], idxs[0], s);
+    launch_compact_staged(at<uint64_t>(ws, L.key), idxs[1], at<uint32_t>(ws, L.bcount), nblk, keys[0], idxs[0], s);
     launch_radix_sort(keys, idxs, cnt + CNT_KEPT, tr->n, at<uint32_t>(ws, L.rcount), s);
     launch_prepare(keys[0], idxs[0], cnt + CNT_KEPT, tr->n, gp, pa->gamma_ref, pa->n_T, nullptr, kexp,
                    at<int4>(ws, L.pos), at<float2>(ws, L.par), nullptr, tr, at<int32_t>(ws, L.su),
@@ -536,7 +549,7 @@ pxc_status pxc_cross_section(pxc_workspace* ws, const pxc_states* st, const pxc_
   }
   launch_segments(at<int4>(ws, L.pos), cnt + CNT_KEPT, nseg, at<int32_t>(ws, L.segr), s);
   launch_items(at<int32_t>(ws, L.segr), nseg, n_c, n_c == 1 ? kItemLines : INT32_MAX / 2, at<int32_t>(ws, L.seg_items),
-               at<Item>(ws, L.items), cnt, L.max_items, s);
+               at<Item>(ws, L.items), cnt, L.max_items, 16ll * profile_ctas(ws, pa->kind), L.max_partial, s);
   ProfP p{};
   p.pos = at<int4>(ws, L.pos);
   p.par = at<float2>(ws, L.par);

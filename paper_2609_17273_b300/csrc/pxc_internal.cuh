@@ -40,10 +40,10 @@ constexpr int kQBlocks = 1184;            // 148 SMs x 8, fixed so the Q reducti
 constexpr int kThreadsQ = 256;
 
 // Profile kernel: segment of S = kThreadsV * kPts grid points per work item.
-constexpr int kThreadsV = 256;
-constexpr int kPts = 8;
+constexpr int kThreadsV = 128;
+constexpr int kPts = 16;
 constexpr int kSeg = kThreadsV * kPts;    // 2048
-constexpr int kStageLines = 256;          // lines per TMA stage (one per thread for the constants)
+constexpr int kStageLines = 256;          // lines per TMA stage (two per thread for the constants)
 constexpr int kStages = 2;
 constexpr int kItemLines = 32768;         // a segment with more lines is split into several items
 constexpr int kPad = kStageLines + 8;     // padding of the per-line arrays so stages never read past them
@@ -57,6 +57,14 @@ struct CondDev {
   float P_f;
   int32_t slot;         // intensity slot (distinct temperature pair)
   int32_t kind;
+};
+
+// Compact per-state record read by the intensity pass for its rejection bound:
+// E exact, g, and log2 of the Boltzmann factor in FP32.
+struct __align__(16) StateFast {
+  double E;
+  int32_t g;
+  float lb;
 };
 
 // Work item of the profile kernel: lines [begin, end) of the sorted list onto
