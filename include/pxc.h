@@ -255,6 +255,26 @@ pxc_status pxc_cross_section_streamed(pxc_workspace* ws, const pxc_states* state
                                       void* dev_chunk_buf0, void* dev_chunk_buf1, size_t dev_chunk_bytes,
                                       float* sigma_out, int32_t* sigma_exp_out, cudaStream_t stream);
 
+/* Partition functions for callers that cannot allocate device memory.
+ * No counterpart in the paper: this is a deployment variant of
+ * pxc_partition_function for code that may not call cudaMalloc at all (a
+ * plug-in inside an application that owns all device memory, a real-time path
+ * that cannot afford cudaMalloc's device-wide synchronisation, a caller with
+ * nowhere to keep a workspace).  It takes no workspace and allocates nothing:
+ * its scratch is a fixed ~1.8 MB array inside the library that every device
+ * loading the library keeps until the process exits.
+ *   n_c <= 64 conditions (PXC_ERR_CAPACITY otherwise); Q_out [n_c] and
+ *   dQ_out [n_c][2] (nullable) as in pxc_partition_function; status_out
+ *   (device int32, nullable) receives PXC_OK, PXC_ERR_NONFINITE or
+ *   PXC_ERR_OVERFLOW once the kernels have run.
+ * All calls share that array: calls overlapping on the GPU (several streams or
+ * host threads) race and must be serialised.  The first call on a device looks
+ * up the array's address with that device current; make it before any stream
+ * capture. */
+pxc_status pxc_partition_function_noalloc(const pxc_states* states, const pxc_condition* c, int32_t n_c,
+                                          double* Q_out, double* dQ_out, int32_t* status_out,
+                                          cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

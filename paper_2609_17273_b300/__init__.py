@@ -73,6 +73,7 @@ ABI_FUNCTIONS = [
     "pxc_set_accumulate", "pxc_partition_function", "pxc_line_intensities", "pxc_cross_section",
     "pxc_cross_section_backward", "pxc_get_stats", "pxc_get_binning", "pxc_stream_buffer_bytes",
     "pxc_cross_section_streamed", "pxc_kernel_launches", "pxc_set_timing", "pxc_get_timing",
+    "pxc_partition_function_noalloc",
 ]
 
 
@@ -102,6 +103,8 @@ def load(path: str = LIB_PATH):
                                              c_ptr, c_ptr, c_ptr]
     L.pxc_get_stats.argtypes = [c_ptr, c_ptr, P(pxc_stats)]
     L.pxc_get_binning.argtypes = [c_ptr, c_ptr, c_ptr, c_ptr, c_ptr]
+    L.pxc_partition_function_noalloc.argtypes = [P(pxc_states), P(pxc_condition), c_i32, c_ptr, c_ptr, c_ptr,
+                                                 c_ptr]
     L.pxc_set_timing.argtypes = [c_ptr, ctypes.c_int]
     L.pxc_get_timing.argtypes = [c_ptr, c_ptr, c_ptr, c_ptr]
     L.pxc_stream_buffer_bytes.argtypes = [c_i64, c_i32, c_i32]
@@ -265,6 +268,19 @@ def pxc_partition_function(ws: Workspace, states: States, conds, stream=None):
     st = states.c()
     _check(load().pxc_partition_function(ws.h, ctypes.byref(st), arr, n, _ptr(Q), _ptr(dQ), _stream(stream)))
     return Q, dQ
+
+
+def pxc_partition_function_noalloc(states: States, conds, stream=None):
+    """Q[n_c], dQ[n_c, 2] and the device status word, with no workspace and no allocation in the library
+    (the output tensors are the caller's).  At most 64 conditions; calls must not overlap on the GPU."""
+    arr, n = _conds(conds)
+    Q = torch.empty(n, dtype=torch.float64, device="cuda")
+    dQ = torch.empty(n, 2, dtype=torch.float64, device="cuda")
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    st = states.c()
+    _check(load().pxc_partition_function_noalloc(ctypes.byref(st), arr, n, _ptr(Q), _ptr(dQ), _ptr(status),
+                                                 _stream(stream)))
+    return Q, dQ, status
 
 
 def pxc_line_intensities(ws: Workspace, states: States, trans: Transitions, cond, grid=None, cutoff: float = 0.0,

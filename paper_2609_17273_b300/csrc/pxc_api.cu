@@ -320,6 +320,10 @@ int profile_ctas(pxc_workspace* ws, int kind) {
 
 }  // namespace
 
+namespace pxc {
+void set_last_error(const char* msg) { snprintf(g_msg, sizeof g_msg, "%s", msg); }
+}  // namespace pxc
+
 extern "C" {
 
 const char* pxc_last_error(void) { return g_msg; }
