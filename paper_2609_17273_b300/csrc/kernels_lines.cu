@@ -777,7 +777,7 @@ __global__ void k_items(const int32_t* __restrict__ segr, int64_t nseg, int n_c,
       unsigned long long all = 0;
       for (int i = 0; i < (int)blockDim.x; ++i) all += part[i];
       long long L = item_lines_max;
-      if (target_items > 0 && item_lines_max < (1 << 30)) {
+      if (target_items > 0) {  // only the single-condition call splits (its partial rows are reduced)
         long long t = (long long)((all + target_items - 1) / target_items);
         long long m = (long long)((all + max_partial - 1) / (max_partial > 0 ? max_partial : 1));
         t = t > 512 ? t : 512;

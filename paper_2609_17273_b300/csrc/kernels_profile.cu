@@ -656,7 +656,12 @@ __global__ void __launch_bounds__(256) k_adjoint(const AdjP p) {
       ga += __shfl_down_sync(0xffffffffu, ga, o);
       gg += __shfl_down_sync(0xffffffffu, gg, o);
     }
-    if (lane == 0) {
+    if (lane == 0 && is == 0.f) {
+      // zero scaled intensity: no contribution to sigma, hence none to any gradient
+      p.lineT[j] = 0.0;
+      p.lineTv[j] = 0.0;
+      p.lineP[j] = 0.0;
+    } else if (lane == 0) {
       const uint32_t t = p.sidx[j];
       double G = 0.0, Da = 0.0, Dg = 0.0;
       const double ccd = cc, ad = alpha, spi = 1.7724538509055160273;

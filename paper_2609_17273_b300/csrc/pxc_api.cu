@@ -553,7 +553,8 @@ pxc_status pxc_cross_section(pxc_workspace* ws, const pxc_states* st, const pxc_
   }
   launch_segments(at<int4>(ws, L.pos), cnt + CNT_KEPT, nseg, at<int32_t>(ws, L.segr), s);
   launch_items(at<int32_t>(ws, L.segr), nseg, n_c, n_c == 1 ? kItemLines : INT32_MAX / 2, at<int32_t>(ws, L.seg_items),
-               at<Item>(ws, L.items), cnt, L.max_items, 16ll * profile_ctas(ws, pa->kind), L.max_partial, s);
+               at<Item>(ws, L.items), cnt, L.max_items, n_c == 1 ? 16ll * profile_ctas(ws, pa->kind) : 0ll,
+               L.max_partial, s);
   ProfP p{};
   p.pos = at<int4>(ws, L.pos);
   p.par = at<float2>(ws, L.par);

@@ -195,6 +195,23 @@ def test_batched_table_matches_oracle_and_plain(pxc):
         assert np.max(np.abs(plain - got)) <= 1e-5 * plain.max()
 
 
+def test_batched_table_with_split_segments_matches_plain(pxc):
+    # enough lines that single-condition calls split dense segments into several items;
+    # the batched call must cover every line of every segment all the same
+    c = H.case("table_1e8", n_trans=3_000_000)
+    conds = [(200.0, 0.0, 1e-5), (1000.0, 0.0, 1.0), (3000.0, 0.0, 100.0)]
+    ws = _ws(pxc, c, n_c=len(conds), n_temps=3)
+    st, tr, prof, grid = H.device(c)
+    sig, e = pxc.pxc_cross_section(ws, st, tr, conds, grid, prof)
+    ws1 = _ws(pxc, c)
+    for i, cond in enumerate(conds):
+        s1, e1 = pxc.pxc_cross_section(ws1, st, tr, cond, grid, prof)
+        plain = H.sigma_phys(s1[0], e1[0].item())
+        got = H.sigma_phys(sig[i], e[i].item())
+        assert np.max(np.abs(plain - got)) <= 1e-5 * np.abs(plain).max(), cond
+    ws.sync()
+
+
 def test_streamed_chunks_match_single_call(pxc):
     import torch
     c = H.case("voigt_1e9", n_states=200_000, n_trans=30_000)
