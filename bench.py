@@ -228,6 +228,19 @@ def main_pxc(args):
                                   sigma_exp=sexp)
         ws.set_accumulate(False)
 
+    # tile configuration of the profile kernel: timed on the first chunk (setup, untimed)
+    tune = None
+    if args.tile < 0:
+        n0 = min(chunk, w.n_trans)
+        tr0 = pxc.Transitions(d_up[:n0], d_lo[:n0], d_A[:n0])
+        pr0 = pxc.Profile(w.profile, w.cutoff, w.mass_da, w.hwhm, d_gr[:n0], d_ne[:n0])
+        t_best, t_ms, _, _ = pxc.pxc_autotune(ws, states, tr0, cond, grid, pr0, w.threshold, repeats=2,
+                                              sigma=sigma.view(1, -1), sigma_exp=sexp)
+        tune = {"tile": t_best, "ms_per_chunk_call": t_ms}
+    else:
+        ws.set_tile(pxc.PROFILES[w.profile], False, args.tile)
+    tile = ws.get_tile(pxc.PROFILES[w.profile], False)
+
     # one counted step: algorithmic eval counts per chunk
     ws.set_accumulate(True)
     sigma.zero_(); sexp.fill_(pxc.PXC_EXP_EMPTY)
@@ -346,7 +359,9 @@ def main_pxc(args):
            "config": {"workload": w.name, "lines": w.n_trans, "states": w.n_states, "grid": w.n_grid,
                       "chunk": chunk, "profile": w.profile, "T": w.T, "P": w.P, "cutoff": w.cutoff,
                       "threshold": w.threshold, "parallelism": f"replicas x{world}",
-                      "l2": "inputs (20 GB) larger than L2", "fp64": "nu, Boltzmann factors, Q"},
+                      "l2": "inputs (20 GB) larger than L2", "fp64": "nu, Boltzmann factors, Q",
+                      "profile_tile": {"tile": tile, "segment_points": pxc.TILE_SEGMENT_POINTS[tile],
+                                       "autotune": tune}},
            "lines_per_s": lines_per_s,
            "counts": {"kept_lines": kept, "evals_nonzero": evals, "evals_window": evals_window},
            "pass_ms_per_step": {"intensity": int_ms / args.steps, "sort": sort_ms / args.steps,
@@ -403,6 +418,7 @@ def run_extras(args, pxc, torch, dev, synth):
                         max_temperatures=nT, device=dev)
     sig = torch.empty(len(conds), w.n_grid, dtype=torch.float32, device=dev)
     se = torch.empty(len(conds), dtype=torch.int32, device=dev)
+    tile_b, tune_b, _, _ = pxc.pxc_autotune(wsb, st, tr, conds, grid, prof, 0.0, repeats=1, sigma=sig, sigma_exp=se)
     ms_b = timed(lambda: pxc.pxc_cross_section(wsb, st, tr, conds, grid, prof, 0.0, sigma=sig, sigma_exp=se))
     sb = wsb.stats()
     del wsb
@@ -415,6 +431,8 @@ def run_extras(args, pxc, torch, dev, synth):
         for c in conds:
             pxc.pxc_cross_section(wsp, st, tr, c, grid, prof, 0.0, sigma=s1, sigma_exp=e1)
 
+    tile_s, _, _, _ = pxc.pxc_autotune(wsp, st, tr, conds[len(conds) // 2], grid, prof, 0.0, repeats=1, sigma=s1,
+                                       sigma_exp=e1)
     ms_s = timed(seq)
     for i in (0, len(conds) // 2, len(conds) - 1):
         pxc.pxc_cross_section(wsp, st, tr, conds[i], grid, prof, 0.0, sigma=s1, sigma_exp=e1)
@@ -423,7 +441,8 @@ def run_extras(args, pxc, torch, dev, synth):
         worst = max(worst, float((a - b).abs().max() / b.abs().max().clamp_min(1e-300)))
     res["batched_table"] = {"workload": w.name, "conditions": len(conds), "lines": w.n_trans,
                             "batched_ms": ms_b, "sequential_ms": ms_s, "speedup": ms_s / ms_b,
-                            "max_abs_diff_rel_peak": worst, "kept_lines": sb["n_kept"]}
+                            "max_abs_diff_rel_peak": worst, "kept_lines": sb["n_kept"],
+                            "tile_batched": tile_b, "autotune_batched_ms": tune_b, "tile_sequential": tile_s}
     del wsp, st, tr, prof, sig
     torch.cuda.empty_cache()
 
@@ -460,6 +479,7 @@ def main():
     ap.add_argument("--workload", default="voigt_1e9")
     ap.add_argument("--lines", type=int, default=0, help="override the transition count (smaller runs)")
     ap.add_argument("--extras-lines", type=int, default=0, help="override the batched-table transition count")
+    ap.add_argument("--tile", type=int, default=-1, help="profile tile configuration (-1: autotune on chunk 0)")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

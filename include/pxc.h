@@ -219,7 +219,7 @@ typedef struct {
   int32_t segment_points;  /* grid points per segment used by the profile kernel */
   int32_t n_segments;
   int32_t I_exp;           /* exponent k of the last condition */
-  int32_t reserved;
+  int32_t tile;            /* profile tile configuration used (0 .. PXC_NUM_TILES-1) */
 } pxc_stats;
 pxc_status pxc_get_stats(pxc_workspace* ws, cudaStream_t stream, pxc_stats* out);
 
@@ -237,6 +237,34 @@ pxc_status pxc_get_binning(pxc_workspace* ws, int64_t* perm_out, int64_t* seg_fi
  * pass, and count[i] the number of timed launches of each (count nullable). */
 pxc_status pxc_set_timing(pxc_workspace* ws, int on);
 pxc_status pxc_get_timing(pxc_workspace* ws, cudaStream_t stream, double* ms, int64_t* count);
+
+/* Profile-kernel tile configurations.  The profile pass (Eq. xsec summed over
+ * the kept lines) splits the grid into segments of S points, one work item per
+ * segment and line range.  The compiled configurations are
+ *   tile 0: S = 128  (32 threads x 4 points, 64 lines per stage)
+ *   tile 1: S = 256  (64 threads x 4 points, 64 lines per stage)
+ *   tile 2: S = 1024 (128 threads x 8 points, 64 lines per stage)
+ *   tile 3: S = 2048 (128 threads x 16 points, 128 lines per stage)
+ * and every one gives the same sigma up to FP32 summation order.  The workspace
+ * keeps one tile per profile kind for single-condition calls (batched = 0,
+ * default tile 0) and one for batched tables (batched = 1, default tile 3). */
+#define PXC_NUM_TILES 4
+pxc_status pxc_set_tile(pxc_workspace* ws, int32_t kind, int32_t batched, int32_t tile);
+pxc_status pxc_get_tile(pxc_workspace* ws, int32_t kind, int32_t batched, int32_t* tile);
+
+/* Autotuner: runs pxc_cross_section with every tile configuration on the
+ * caller's own inputs (same arguments as pxc_cross_section), `repeats` timed
+ * runs each after one warm-up run, times each run with CUDA events on
+ * `stream`, and keeps the fastest tile in the workspace for this profile kind
+ * and for single (n_c == 1) or batched (n_c > 1) calls.  ms_out [PXC_NUM_TILES]
+ * (host, nullable) receives each tile's mean milliseconds per call; *tile_out
+ * (host, nullable) the tile chosen.  sigma_out / sigma_exp_out end holding the
+ * result of the chosen tile.  Synchronises `stream`. */
+pxc_status pxc_autotune(pxc_workspace* ws, const pxc_states* states, const pxc_transitions* trans,
+                        const pxc_condition* c, int32_t n_c, const pxc_grid* grid,
+                        const pxc_profile_args* prof, double threshold, float* sigma_out,
+                        int32_t* sigma_exp_out, int32_t repeats, int32_t* tile_out, double* ms_out,
+                        cudaStream_t stream);
 
 /* Stream a HOST-resident line list through the device in chunks of
  * cap.max_lines transitions (Sec. 2.1: bounded-memory streaming of large

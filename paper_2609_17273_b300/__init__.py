@@ -56,7 +56,7 @@ class pxc_capacity(ctypes.Structure):
 
 class pxc_stats(ctypes.Structure):
     _fields_ = [("n_kept", c_i64), ("n_nonzero", c_i64), ("evals_window", c_i64), ("evals_nonzero", c_i64),
-                ("segment_points", c_i32), ("n_segments", c_i32), ("I_exp", c_i32), ("reserved", c_i32)]
+                ("segment_points", c_i32), ("n_segments", c_i32), ("I_exp", c_i32), ("tile", c_i32)]
 
 
 class PxcError(RuntimeError):
@@ -73,15 +73,20 @@ ABI_FUNCTIONS = [
     "pxc_set_accumulate", "pxc_partition_function", "pxc_line_intensities", "pxc_cross_section",
     "pxc_cross_section_backward", "pxc_get_stats", "pxc_get_binning", "pxc_stream_buffer_bytes",
     "pxc_cross_section_streamed", "pxc_kernel_launches", "pxc_set_timing", "pxc_get_timing",
-    "pxc_partition_function_noalloc",
+    "pxc_partition_function_noalloc", "pxc_set_tile", "pxc_get_tile", "pxc_autotune",
 ]
 
+# Profile-kernel tile configurations (segment width in grid points), as compiled into the library.
+NUM_TILES = 4
+TILE_SEGMENT_POINTS = (128, 256, 1024, 2048)
 
-def load(path: str = LIB_PATH):
-    """Load libpxc.so; raises if it has not been built (no fallback path exists)."""
+
+def load(path: str | None = None):
+    """Load libpxc.so (or the build named by PXC_LIBRARY); raises if it has not been built."""
     global _lib
     if _lib is not None:
         return _lib
+    path = path or os.environ.get("PXC_LIBRARY") or LIB_PATH
     if not os.path.exists(path):
         raise ImportError(f"libpxc.so not built ({path}); run paper_2609_17273_b300/build.py")
     L = ctypes.CDLL(path)
@@ -107,6 +112,10 @@ def load(path: str = LIB_PATH):
                                                  c_ptr]
     L.pxc_set_timing.argtypes = [c_ptr, ctypes.c_int]
     L.pxc_get_timing.argtypes = [c_ptr, c_ptr, c_ptr, c_ptr]
+    L.pxc_set_tile.argtypes = [c_ptr, c_i32, c_i32, c_i32]
+    L.pxc_get_tile.argtypes = [c_ptr, c_i32, c_i32, P(c_i32)]
+    L.pxc_autotune.argtypes = [c_ptr, P(pxc_states), P(pxc_transitions), P(pxc_condition), c_i32, P(pxc_grid),
+                               P(pxc_profile_args), c_dbl, c_ptr, c_ptr, c_i32, P(c_i32), c_ptr, c_ptr]
     L.pxc_stream_buffer_bytes.argtypes = [c_i64, c_i32, c_i32]
     L.pxc_stream_buffer_bytes.restype = ctypes.c_size_t
     L.pxc_cross_section_streamed.argtypes = [c_ptr, P(pxc_states), c_ptr, c_ptr, c_ptr, c_i32, c_ptr, c_ptr, c_i64,
@@ -259,6 +268,15 @@ class Workspace:
     def set_accumulate(self, on: bool):
         _check(load().pxc_set_accumulate(self.h, int(on)))
 
+    def set_tile(self, kind: int, batched: bool, tile: int):
+        """Profile-kernel tile for this kind and for single-condition (batched=False) or batched calls."""
+        _check(load().pxc_set_tile(self.h, int(kind), int(bool(batched)), int(tile)))
+
+    def get_tile(self, kind: int, batched: bool) -> int:
+        t = c_i32(0)
+        _check(load().pxc_get_tile(self.h, int(kind), int(bool(batched)), ctypes.byref(t)))
+        return int(t.value)
+
 
 def pxc_partition_function(ws: Workspace, states: States, conds, stream=None):
     """Q[n_c] (float64) and dQ[n_c, 2] on the device."""
@@ -314,6 +332,26 @@ def pxc_cross_section(ws: Workspace, states: States, trans: Transitions, conds, 
     _check(load().pxc_cross_section(ws.h, ctypes.byref(st), ctypes.byref(tr), arr, n_c, ctypes.byref(g),
                                     ctypes.byref(pa), threshold, _ptr(sigma), _ptr(sigma_exp), _stream(stream)))
     return sigma, sigma_exp
+
+
+def pxc_autotune(ws: Workspace, states: States, trans: Transitions, conds, grid, profile: Profile,
+                 threshold: float = 0.0, repeats: int = 3, sigma=None, sigma_exp=None, stream=None):
+    """Times every tile configuration on these inputs and keeps the fastest in the workspace.
+    Returns (tile, [ms per call for each tile], sigma, exp); sigma/exp hold the chosen tile's result."""
+    arr, n_c = _conds(conds)
+    ng = int(grid[2])
+    if sigma is None:
+        sigma = torch.empty(n_c, ng, dtype=torch.float32, device="cuda")
+    if sigma_exp is None:
+        sigma_exp = torch.empty(n_c, dtype=torch.int32, device="cuda")
+    g = pxc_grid(*grid)
+    st, tr, pa = states.c(), trans.c(), profile.c()
+    tile = c_i32(-1)
+    ms = (ctypes.c_double * NUM_TILES)()
+    _check(load().pxc_autotune(ws.h, ctypes.byref(st), ctypes.byref(tr), arr, n_c, ctypes.byref(g),
+                               ctypes.byref(pa), threshold, _ptr(sigma), _ptr(sigma_exp), int(repeats),
+                               ctypes.byref(tile), ms, _stream(stream)))
+    return int(tile.value), list(ms), sigma, sigma_exp
 
 
 def pxc_cross_section_backward(ws: Workspace, states: States, trans: Transitions, cond, grid, profile: Profile,

@@ -69,14 +69,14 @@ void launch_sorted_intensity(const int32_t* su, const int32_t* sl, const double*
 void launch_scale(const double* sI, const unsigned long long* n_dev, int64_t n_max, const int32_t* kexp,
                   float* Is, unsigned long long* counters, cudaStream_t s);
 
-void launch_segments(const int4* pos, const unsigned long long* n_dev, int64_t nseg, int32_t* segr,
+void launch_segments(const int4* pos, const unsigned long long* n_dev, int64_t nseg, int seg, int32_t* segr,
                      cudaStream_t s);
 
 void launch_items(const int32_t* segr, int64_t nseg, int n_c, int item_lines, int32_t* seg_items,
                   Item* items, unsigned long long* counters, int64_t max_items, int64_t target_items,
                   int64_t max_partial, cudaStream_t s);
 
-void launch_reduce_partials(const Item* items, const int32_t* seg_items, int64_t nseg, int n_c,
+void launch_reduce_partials(const Item* items, const int32_t* seg_items, int64_t nseg, int seg, int n_c,
                             const float* partial, float* sigma, int64_t n_grid, cudaStream_t s);
 
 void launch_stick_out(const double* Iv, const uint64_t* key, int64_t n, const int32_t* kexp, float* I_scaled,
@@ -93,7 +93,7 @@ struct ProfP {
   const unsigned long long* n_items;
   unsigned long long* queue;
   float* sigma;            // [n_c][n_grid]
-  float* partial;          // [max_partial][kSeg]
+  float* partial;          // partial rows of the segment width in use
   int64_t n_grid;
   double nu_min, dnu;
   int accumulate;
@@ -101,8 +101,9 @@ struct ProfP {
   unsigned* err;
   long long spin_limit;
 };
-void launch_profile(const ProfP& p, int grid_ctas, cudaStream_t s);
-int profile_occupancy(int kind);
+void launch_profile(const ProfP& p, int tile, int grid_ctas, cudaStream_t s);
+int profile_occupancy(int kind, int tile);
+int tile_seg(int tile);
 
 struct AdjP {
   const int4* pos;

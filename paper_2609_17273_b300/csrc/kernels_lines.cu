@@ -728,11 +728,11 @@ void launch_scale(const double* sI, const unsigned long long* n_dev, int64_t n_m
 // Windows are monotone in nu, so the lines meeting segment s = [s S, (s+1) S) are the
 // contiguous sorted range [first, last): first = #lines with ihi < s S, last = #lines with ilo <= (s+1) S - 1.
 __global__ void k_segments(const int4* __restrict__ pos, const unsigned long long* __restrict__ n_dev, int64_t nseg,
-                           int32_t* __restrict__ segr) {
+                           int seg, int32_t* __restrict__ segr) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nseg) return;
   const int64_t n = (int64_t)*n_dev;
-  const int64_t a = s * kSeg, b = (s + 1) * kSeg - 1;
+  const int64_t a = s * seg, b = (s + 1) * seg - 1;
   int64_t lo = 0, hi = n;
   while (lo < hi) {
     int64_t m = (lo + hi) >> 1;
@@ -748,8 +748,9 @@ __global__ void k_segments(const int4* __restrict__ pos, const unsigned long lon
   segr[nseg + s] = (int32_t)lo;
 }
 
-void launch_segments(const int4* pos, const unsigned long long* n_dev, int64_t nseg, int32_t* segr, cudaStream_t s) {
-  k_segments<<<(unsigned)((nseg + 255) / 256), 256, 0, s>>>(pos, n_dev, nseg, segr);
+void launch_segments(const int4* pos, const unsigned long long* n_dev, int64_t nseg, int seg, int32_t* segr,
+                     cudaStream_t s) {
+  k_segments<<<(unsigned)((nseg + 255) / 256), 256, 0, s>>>(pos, n_dev, nseg, seg, segr);
   note_launches(1);
 }
 
@@ -844,23 +845,24 @@ void launch_items(const int32_t* segr, int64_t nseg, int n_c, int item_lines, in
 
 // Adds the partial rows of split segments to sigma, in item order (deterministic).
 __global__ void k_reduce_partials(const Item* __restrict__ items, const int32_t* __restrict__ seg_items, int64_t nseg,
-                                  const float* __restrict__ partial, float* __restrict__ sigma, int64_t n_grid) {
+                                  int seg, const float* __restrict__ partial, float* __restrict__ sigma,
+                                  int64_t n_grid) {
   int64_t gi = blockIdx.x;
   int32_t f = seg_items[gi], e = seg_items[gi + 1];
   if (e - f <= 1) return;
   int64_t s = gi % nseg, c = gi / nseg;
-  for (int p = threadIdx.x; p < kSeg; p += blockDim.x) {
-    int64_t i = s * kSeg + p;
+  for (int p = threadIdx.x; p < seg; p += blockDim.x) {
+    int64_t i = s * seg + p;
     if (i >= n_grid) break;
     float v = sigma[c * n_grid + i];
-    for (int32_t it = f + 1; it < e; ++it) v += partial[(int64_t)items[it].slot * kSeg + p];
+    for (int32_t it = f + 1; it < e; ++it) v += partial[(int64_t)items[it].slot * seg + p];
     sigma[c * n_grid + i] = v;
   }
 }
 
-void launch_reduce_partials(const Item* items, const int32_t* seg_items, int64_t nseg, int n_c,
+void launch_reduce_partials(const Item* items, const int32_t* seg_items, int64_t nseg, int seg, int n_c,
                             const float* partial, float* sigma, int64_t n_grid, cudaStream_t s) {
-  k_reduce_partials<<<(unsigned)(nseg * n_c), 256, 0, s>>>(items, seg_items, nseg, partial, sigma, n_grid);
+  k_reduce_partials<<<(unsigned)(nseg * n_c), 128, 0, s>>>(items, seg_items, nseg, seg, partial, sigma, n_grid);
   note_launches(1);
 }
 

@@ -1,14 +1,14 @@
 // Profile accumulation (Eq. xsec over the kept lines) and its adjoint.
 //
-// Forward: persistent CTAs take work items (condition, grid segment of kSeg
-// points, a contiguous range of the nu-sorted lines whose windows meet the
-// segment).  Thread t owns the points t + 256 q, q < kPts, in registers.  The
-// line records (position, broadening parameters, scaled intensity) are staged
-// into shared memory by 1-D bulk TMA copies (cp.async.bulk) completing on an
-// mbarrier, kStages buffers deep; every wait is bounded.  Per stage, each thread
-// turns one record into the line's constants, then every thread evaluates all
-// staged lines at its points (FP32, no atomics).  Stage sums are folded into a
-// compensated (two-sum) accumulator.
+// Forward: persistent CTAs take work items (condition, grid segment of S points,
+// a contiguous range of the nu-sorted lines whose windows meet the segment);
+// S and the CTA shape are one of the compiled tile configurations.  Each lane
+// owns points of the segment in registers.  The line records (position,
+// broadening parameters, scaled intensity) are staged into shared memory by
+// 1-D bulk TMA copies (cp.async.bulk) completing on mbarriers; every wait is
+// bounded.  Each warp turns the staged records into its own line constants and
+// classes and evaluates its lines at its points in FP32, with no atomics; stage
+// sums are added into per-item sums (two-level summation).
 //
 // Voigt uses Humlicek's W4 rational approximation of the Faddeeva function
 // (J. Humlicek, JQSRT 27 (1982) 437), the method the paper recommends for GPU
@@ -206,25 +206,22 @@ __device__ __forceinline__ float w4_re(float x, float y) {
 }
 
 // ------------------------------------------------------------------ forward kernel
-// Warp w of a CTA owns the points [512 w, 512 w + 512) of the CTA's segment; lane l holds
-// the points 256 w + l + 32 k, k < kPts.  For every staged line one thread precomputes two
-// 8-bit masks over the warps: `fast` (the warp's points all lie inside the cut-off window and
-// in W4 region I, so the branch-free far-wing formula applies with no mask) and `touch` (the
-// window meets the warp's points).  A warp tests its bits once per line.
-constexpr int kWarpPts = 32 * kPts;          // 512 points per warp
-constexpr int kWarps = kThreadsV / 32;
+// A CTA of THREADS threads takes work items on a segment of SEG = THREADS * PTS grid
+// points.  Warp w owns the points [32 PTS w, 32 PTS (w + 1)); lane l holds the points
+// 32 PTS w + l + 32 k, k < PTS, in registers.  The segment width and the lines per stage
+// are template parameters: the tile configurations below are compiled, and the workspace
+// picks one per profile kind (pxc_autotune times them on the caller's inputs).
 
 struct __align__(16) LineC {
   float pf, step, nfs, B1;     // centre offset (grid steps, exact integer part), step, -f*step, 2y^2-1 | gamma^2
   float A2, K, KA, y;          // region-I constants (Voigt), Lorentz/Gauss amplitude in K
   int lo, hi;                  // window relative to the segment (grid points, clamped)
-  int masks;                   // bits 0-7 fast warps, 8-15 far warps with a window edge, 16-23 warps near the core
+  int masks;                   // 1 if the line is valid with non-zero intensity and a non-empty window; then its class
   float Kc;                    // amplitude of the general path
   float reach, cen;            // half-width of the non-region-I zone and the centre (grid steps)
   float pad0, pad1;
 };
 
-constexpr int kStageBytes = kStageLines * (16 + 8 + 4);
 // Smallest Doppler HWHM used (cm^-1).  Keeps the scaled FP32 arithmetic finite for lines with
 // nu below ~0.05 cm^-1, whose true alpha is far below both the grid step and gamma: the
 // sampled profile changes by less than (alpha/gamma)^2 off the line centre.
@@ -232,7 +229,7 @@ constexpr float kAlphaMin = 8.4e-8f;
 // Smallest Lorentz HWHM used (cm^-1): gamma^2 stays a normal FP32 number.
 constexpr float kGammaMin = 1e-15f;
 
-template <int KIND>
+template <int KIND, int SEG>
 __device__ __forceinline__ void line_constants(const int4 p4, const float2 pr, const float is, const CondDev& cd,
                                                int64_t i0, float dnu_f, double nu_min, double dnu, bool valid,
                                                LineC& c) {
@@ -241,7 +238,7 @@ __device__ __forceinline__ void line_constants(const int4 p4, const float2 pr, c
   c.pf = (float)((int64_t)ic - i0);
   const int64_t lo = (int64_t)p4.z - i0, hi = (int64_t)p4.w - i0;
   c.lo = (int)(lo < 0 ? 0 : lo);
-  c.hi = (int)(hi > kSeg - 1 ? kSeg - 1 : hi);
+  c.hi = (int)(hi > SEG - 1 ? SEG - 1 : hi);
   const float cen = c.pf + f;  // line centre in grid steps from the segment start
   float reach = 0.f;           // half-width (grid steps) of the zone needing the general path
   if (KIND == PXC_LORENTZ) {
@@ -280,32 +277,29 @@ __device__ __forceinline__ void line_constants(const int4 p4, const float2 pr, c
       // provably-zero trim: 2^(-t) for t > 159 is below the FP32 range of every product here
       const float r = 12.7f / c.step;        // |X'| <= 12.7 <=> X^2 <= 111.8
       const float elo = ceilf(cen - r), ehi = floorf(cen + r);
-      if (elo > (float)c.lo) c.lo = (int)fminf(elo, (float)kSeg);
+      if (elo > (float)c.lo) c.lo = (int)fminf(elo, (float)SEG);
       if (ehi < (float)c.hi) c.hi = (int)fmaxf(ehi, -1.f);
     }
   }
-  // Per warp: fast (inside the window and in region I), far-but-partial (region I, window edge
-  // among the warp's points: same formula with a lane mask), slow (the line core is near).
-  int fast = 0, fmask = 0, slow = 0;
-  if (valid && is != 0.f && c.lo <= c.hi) {
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) {
-      const int a = w * kWarpPts, b = a + kWarpPts - 1;
-      if (c.hi < a || c.lo > b) continue;
-      const bool full = c.lo <= a && c.hi >= b;
-      bool far = true;
-      if (KIND == PXC_VOIGT) {
-        const float dmin = fmaxf(0.f, fmaxf(cen - (float)b, (float)a - cen));
-        far = dmin > reach;
-      }
-      if (!far) slow |= 1 << w;
-      else if (full) fast |= 1 << w;
-      else fmask |= 1 << w;
-    }
-  }
-  c.masks = fast | (fmask << 8) | (slow << 16);
   c.reach = reach;
   c.cen = cen;
+  c.masks = (valid && is != 0.f && c.lo <= c.hi) ? 1 : 0;
+}
+
+// Class of a line for the warp owning points [a, a + WPTS) of the segment:
+// 0 nothing, 1 fast (inside the window, region I), 2 window edge (region I, lane mask),
+// 3 near the line core.
+template <int KIND, int WPTS>
+__device__ __forceinline__ int line_class(const LineC& c, int a) {
+  const int b = a + WPTS - 1;
+  if (!c.masks || c.hi < a || c.lo > b) return 0;
+  bool far = true;
+  if (KIND == PXC_VOIGT) {
+    const float dmin = fmaxf(0.f, fmaxf(c.cen - (float)b, (float)a - c.cen));
+    far = dmin > c.reach;
+  }
+  if (!far) return 3;
+  return (c.lo <= a && c.hi >= b) ? 1 : 2;
 }
 
 template <int KIND>
@@ -315,8 +309,8 @@ __device__ __forceinline__ float eval_general(float x, const LineC& c) {
   return c.K * fex2(-(x * x));
 }
 
-// Branch-free evaluation of one line at the lane's kPts points (fast warps).
-template <int KIND>
+// Branch-free evaluation of one line at the lane's PTS points (fast class).
+template <int KIND, int PTS>
 __device__ __forceinline__ void eval_fast(const LineC& c, float lane_f, float* acc) {
   if (KIND == PXC_VOIGT) {
     // far wing, W4 region I: Re w = y (A + x^2) / (sqrt(pi) ((A - x^2)^2 + 4 x^2 y^2)), A = 1/2 + y^2;
@@ -326,7 +320,7 @@ __device__ __forceinline__ void eval_fast(const LineC& c, float lane_f, float* a
     const float x0 = fmaf(lane_f - f0.x, f0.y, f0.z);
     const float s32 = 32.f * f0.y;
 #pragma unroll
-    for (int k = 0; k < kPts; ++k) {
+    for (int k = 0; k < PTS; ++k) {
       const float x = fmaf((float)k, s32, x0);
       const float x2 = x * x;
       const float den = fmaf(x2, x2 + f0.w, f1.x);
@@ -337,7 +331,7 @@ __device__ __forceinline__ void eval_fast(const LineC& c, float lane_f, float* a
     const float4 f0 = *reinterpret_cast<const float4*>(&c.pf);
     const float K = c.K;
 #pragma unroll
-    for (int k = 0; k < kPts; ++k) {
+    for (int k = 0; k < PTS; ++k) {
       const float x = fmaf(lane_f + (float)(32 * k) - f0.x, f0.y, f0.z);
       if (KIND == PXC_LORENTZ) acc[k] = fmaf(K, frcp(fmaf(x, x, f0.w)), acc[k]);
       else acc[k] = fmaf(K, fex2(-(x * x)), acc[k]);
@@ -346,7 +340,7 @@ __device__ __forceinline__ void eval_fast(const LineC& c, float lane_f, float* a
 }
 
 // Two lines at once (more independent work per point, half the loop overhead).
-template <int KIND>
+template <int KIND, int PTS>
 __device__ __forceinline__ void eval_fast2(const LineC& c, const LineC& d, float lane_f, float* acc) {
   if (KIND == PXC_VOIGT) {
     const float4 a0 = *reinterpret_cast<const float4*>(&c.pf), a1 = *reinterpret_cast<const float4*>(&c.A2);
@@ -354,20 +348,20 @@ __device__ __forceinline__ void eval_fast2(const LineC& c, const LineC& d, float
     const float xa = fmaf(lane_f - a0.x, a0.y, a0.z), sa = 32.f * a0.y;
     const float xb = fmaf(lane_f - b0.x, b0.y, b0.z), sb = 32.f * b0.y;
 #pragma unroll
-    for (int k = 0; k < kPts; ++k) {
+    for (int k = 0; k < PTS; ++k) {
       const float x = fmaf((float)k, sa, xa), y = fmaf((float)k, sb, xb);
       const float x2 = x * x, y2 = y * y;
       const float ra = frcp(fmaf(x2, x2 + a0.w, a1.x)), rb = frcp(fmaf(y2, y2 + b0.w, b1.x));
       acc[k] = fmaf(fmaf(x2, a1.y, a1.z), ra, fmaf(fmaf(y2, b1.y, b1.z), rb, acc[k]));
     }
   } else {
-    eval_fast<KIND>(c, lane_f, acc);
-    eval_fast<KIND>(d, lane_f, acc);
+    eval_fast<KIND, PTS>(c, lane_f, acc);
+    eval_fast<KIND, PTS>(d, lane_f, acc);
   }
 }
 
 // Far-wing formula with a lane mask (the window ends among this warp's points).
-template <int KIND>
+template <int KIND, int PTS>
 __device__ __forceinline__ void eval_fastmask(const LineC& c, int wbase, int lane, float* acc) {
   const unsigned span = (unsigned)(c.hi - c.lo);
   const int rel0 = wbase + lane - c.lo;
@@ -375,7 +369,7 @@ __device__ __forceinline__ void eval_fastmask(const LineC& c, int wbase, int lan
     const float x0 = fmaf((float)(wbase + lane) - c.pf, c.step, c.nfs);
     const float s32 = 32.f * c.step;
 #pragma unroll
-    for (int k = 0; k < kPts; ++k) {
+    for (int k = 0; k < PTS; ++k) {
       const float x = fmaf((float)k, s32, x0);
       const float x2 = x * x;
       const float den = fmaf(x2, x2 + c.B1, c.A2);
@@ -384,7 +378,7 @@ __device__ __forceinline__ void eval_fastmask(const LineC& c, int wbase, int lan
     }
   } else {
 #pragma unroll
-    for (int k = 0; k < kPts; ++k) {
+    for (int k = 0; k < PTS; ++k) {
       const float x = fmaf((float)(wbase + lane + 32 * k) - c.pf, c.step, c.nfs);
       const float v = KIND == PXC_LORENTZ ? c.K * frcp(fmaf(x, x, c.B1)) : c.K * fex2(-(x * x));
       acc[k] += (unsigned)(rel0 + 32 * k) <= span ? v : 0.f;
@@ -398,7 +392,7 @@ __device__ __forceinline__ void eval_fastmask(const LineC& c, int wbase, int lan
 // (N cubic, D monic quartic, coefficients from Y = y^2 once per line and warp; Humlicek's
 // constants satisfy a = 2.5 b, which gives the factored forms below); only |x|+y < 5.5
 // needs the complex regions III/IV.
-template <int KIND>
+template <int KIND, int PTS>
 __device__ __forceinline__ void eval_slow(const LineC& c, int wbase, int lane, float* acc) {
   const unsigned span = (unsigned)(c.hi - c.lo);
   const float bq = 0.5641896f;
@@ -409,7 +403,7 @@ __device__ __forceinline__ void eval_slow(const LineC& c, int wbase, int lane, f
   const float d0 = (((Y + 6.f) * Y + 10.5f) * Y + 4.5f) * Y + 0.5625f;
   const float Ky = c.Kc * c.y;
 #pragma unroll
-  for (int k = 0; k < kPts; ++k) {
+  for (int k = 0; k < PTS; ++k) {
     const int b0 = wbase + 32 * k;
     if (b0 > c.hi || b0 + 31 < c.lo) continue;
     const int li = b0 + lane;
@@ -431,173 +425,220 @@ __device__ __forceinline__ void eval_slow(const LineC& c, int wbase, int lane, f
   }
 }
 
-template <int KIND>
-__global__ void __launch_bounds__(kThreadsV, 4) k_profile(const ProfP p) {
+// Forward kernel.  The CTA's warps share kNB bulk-copy stage buffers of SL lines; each
+// warp turns every staged record into its own line constants and class (so no CTA barrier
+// is needed inside a work item), keeping two in-order lists in private shared memory: the
+// fast lines from the front, the others from the back.  The last warp to finish reading a
+// stage buffer re-arms it with the copy kNB stages ahead, so warps drift apart by up to
+// kNB - 1 stages instead of waiting for each other at every stage.
+constexpr int kNB = 3;
+
+template <int THREADS, int SL>
+constexpr size_t profile_smem() {
+  return (size_t)kNB * SL * (16 + 8 + 4) + (size_t)(THREADS / 32) * SL * sizeof(LineC);
+}
+
+template <int KIND, int THREADS, int PTS, int SL, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k_profile(const ProfP p) {
+  constexpr int SEG = THREADS * PTS, WPTS = 32 * PTS, NW = THREADS / 32;
+  constexpr int SBYTES = SL * (16 + 8 + 4);
   extern __shared__ __align__(128) unsigned char dyn_smem[];
-  unsigned char (*raw)[kStageBytes] = reinterpret_cast<unsigned char (*)[kStageBytes]>(dyn_smem);
-  LineC* lc = reinterpret_cast<LineC*>(dyn_smem + kStages * kStageBytes);
-  // per warp, the staged lines it evaluates, in line order: fast ones, then the others
-  uint16_t* lists = reinterpret_cast<uint16_t*>(dyn_smem + kStages * kStageBytes + kStageLines * sizeof(LineC));
-  __shared__ __align__(8) uint64_t bar[kStages];
-  __shared__ Item item_sh;
+  unsigned char* raw = dyn_smem;                                              // [kNB][SBYTES]
+  LineC* wl = reinterpret_cast<LineC*>(dyn_smem + kNB * SBYTES);             // [NW][SL]
+  __shared__ __align__(8) uint64_t full[kNB];
+  __shared__ int consumed[kNB];
+  __shared__ int issued[kNB];
+  __shared__ Item item_sh[2];
+  __shared__ int abort_sh;
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  const int wbase = warp * kWarpPts;
+  const int wbase = warp * WPTS;
   const float lane_f = (float)(wbase + lane);
-  const int wbit = 1 << warp, mbit = 1 << (warp + 8), sbit = 1 << (warp + 16);
+  const unsigned lt = (1u << lane) - 1u;
+  LineC* my = wl + warp * SL;
   if (tid == 0) {
-    for (int b = 0; b < kStages; ++b) mbar_init(&bar[b], 1);
+    for (int b = 0; b < kNB; ++b) { mbar_init(&full[b], 1); consumed[b] = 0; issued[b] = 0; }
     fence_mbar_init();
+    abort_sh = 0;
   }
   __syncthreads();
-  unsigned phase = 0;  // bit b: parity to wait for on buffer b
+  unsigned phase = 0;  // bit b: parity this warp waits for next on buffer b
   const unsigned long long n_items = *p.n_items;
   const float dnu_f = (float)p.dnu;
 
-  for (;;) {
+  for (int iter = 0;; ++iter) {
     if (tid == 0) {
       unsigned long long it = atomicAdd(p.queue, 1ull);
-      if (it < n_items) item_sh = p.items[it]; else item_sh.cond = -1;
+      if (it < n_items && !abort_sh) item_sh[iter & 1] = p.items[it]; else item_sh[iter & 1].cond = -1;
     }
-    __syncthreads();
-    const Item item = item_sh;
+    __syncthreads();  // also: every warp has finished the previous item, so all stage buffers are free
+    const Item item = item_sh[iter & 1];
     if (item.cond < 0) break;
     const CondDev cd = p.cond[item.cond];
-    const int64_t i0 = (int64_t)item.seg * kSeg;
+    const int64_t i0 = (int64_t)item.seg * SEG;
     const float* Is = p.Is + (int64_t)cd.slot * p.is_stride;
     const int j0 = item.begin & ~3;
-    const int nst = item.end > item.begin ? (item.end - j0 + kStageLines - 1) / kStageLines : 0;
+    const int nst = item.end > item.begin ? (item.end - j0 + SL - 1) / SL : 0;
 
-    float sum[kPts];
+    float sum[PTS];
 #pragma unroll
-    for (int k = 0; k < kPts; ++k) sum[k] = 0.f;
+    for (int k = 0; k < PTS; ++k) sum[k] = 0.f;
 
     auto issue = [&](int st) {
-      const int b = st % kStages;
-      const int64_t J = (int64_t)j0 + (int64_t)st * kStageLines;
-      mbar_expect_tx(&bar[b], kStageBytes);
-      bulk_g2s(raw[b], p.pos + J, kStageLines * 16, &bar[b]);
-      bulk_g2s(raw[b] + kStageLines * 16, p.par + J, kStageLines * 8, &bar[b]);
-      bulk_g2s(raw[b] + kStageLines * 24, Is + J, kStageLines * 4, &bar[b]);
+      const int b = st % kNB;
+      const int64_t J = (int64_t)j0 + (int64_t)st * SL;
+      unsigned char* dst = raw + b * SBYTES;
+      issued[b] += 1;
+      mbar_expect_tx(&full[b], SBYTES);
+      bulk_g2s(dst, p.pos + J, SL * 16, &full[b]);
+      bulk_g2s(dst + SL * 16, p.par + J, SL * 8, &full[b]);
+      bulk_g2s(dst + SL * 24, Is + J, SL * 4, &full[b]);
     };
     if (tid == 0) {
       fence_proxy_async();
-      for (int st = 0; st < kStages && st < nst; ++st) issue(st);
+      for (int st = 0; st < kNB && st < nst; ++st) issue(st);
     }
 
     bool aborted = false;
     for (int st = 0; st < nst; ++st) {
-      const int b = st % kStages;
-      const bool ok = mbar_wait_bounded(&bar[b], (phase >> b) & 1u, p.spin_limit);
+      const int b = st % kNB;
+      const bool ok = mbar_wait_bounded(&full[b], (phase >> b) & 1u, p.spin_limit);
       phase ^= 1u << b;
-      if (__syncthreads_or(!ok)) { aborted = true; break; }
-#pragma unroll
-      for (int r = 0; r < kStageLines / kThreadsV; ++r) {
-        const int j = tid + r * kThreadsV;
-        const int64_t J = (int64_t)j0 + (int64_t)st * kStageLines + j;
-        const int4 p4 = reinterpret_cast<const int4*>(raw[b])[j];
-        const float2 pr = reinterpret_cast<const float2*>(raw[b] + kStageLines * 16)[j];
-        const float is = reinterpret_cast<const float*>(raw[b] + kStageLines * 24)[j];
-        LineC c;
-        line_constants<KIND>(p4, pr, is, cd, i0, dnu_f, p.nu_min, p.dnu, J >= item.begin && J < item.end, c);
-        lc[j] = c;
-      }
-      __syncthreads();
-      if (tid == 0 && st + kStages < nst) {
-        fence_proxy_async();
-        issue(st + kStages);
-      }
-      float acc[kPts];
-#pragma unroll
-      for (int k = 0; k < kPts; ++k) acc[k] = 0.f;
-      // this warp's lines of the stage, compacted in line order
-      uint16_t* fl = lists + warp * 2 * kStageLines;
-      uint16_t* ol = fl + kStageLines;
+      if (__any_sync(0xffffffffu, !ok)) { aborted = true; break; }
+      // this warp's constants and classes for the staged lines, compacted in line order
+      const unsigned char* src = raw + b * SBYTES;
       int nf = 0, no = 0;
-      const unsigned lt = (1u << lane) - 1u;
-#pragma unroll 2
-      for (int c0 = 0; c0 < kStageLines; c0 += 32) {
-        const int m = lc[c0 + lane].masks;
-        const unsigned bf = __ballot_sync(0xffffffffu, (m & wbit) != 0);
-        const unsigned bo = __ballot_sync(0xffffffffu, (m & (mbit | sbit)) != 0);
-        if (m & wbit) fl[nf + __popc(bf & lt)] = (uint16_t)(c0 + lane);
-        if (m & (mbit | sbit)) ol[no + __popc(bo & lt)] = (uint16_t)(c0 + lane);
+#pragma unroll
+      for (int r = 0; r < SL / 32; ++r) {
+        const int j = lane + 32 * r;
+        const int64_t J = (int64_t)j0 + (int64_t)st * SL + j;
+        const int4 p4 = reinterpret_cast<const int4*>(src)[j];
+        const float2 pr = reinterpret_cast<const float2*>(src + SL * 16)[j];
+        const float is = reinterpret_cast<const float*>(src + SL * 24)[j];
+        LineC c;
+        line_constants<KIND, SEG>(p4, pr, is, cd, i0, dnu_f, p.nu_min, p.dnu, J >= item.begin && J < item.end, c);
+        const int cls = line_class<KIND, WPTS>(c, wbase);
+        c.masks = cls;
+        const unsigned bf = __ballot_sync(0xffffffffu, cls == 1);
+        const unsigned bo = __ballot_sync(0xffffffffu, cls >= 2);
+        if (cls == 1) my[nf + __popc(bf & lt)] = c;
+        if (cls >= 2) my[SL - 1 - (no + __popc(bo & lt))] = c;
         nf += __popc(bf);
         no += __popc(bo);
       }
       __syncwarp();
+      // release the stage buffer; the last warp re-arms it
+      if (lane == 0) {
+        __threadfence_block();
+        if (atomicAdd(&consumed[b], 1) == NW - 1) {
+          consumed[b] = 0;
+          __threadfence_block();
+          if (st + kNB < nst) {
+            fence_proxy_async();
+            issue(st + kNB);
+          }
+        }
+      }
+      float acc[PTS];
+#pragma unroll
+      for (int k = 0; k < PTS; ++k) acc[k] = 0.f;
       int i = 0;
-      for (; i + 1 < nf; i += 2) eval_fast2<KIND>(lc[fl[i]], lc[fl[i + 1]], lane_f, acc);
-      if (i < nf) eval_fast<KIND>(lc[fl[i]], lane_f, acc);
-      for (int j = 0; j < no; ++j) {
-        const LineC& c = lc[ol[j]];
-        if (c.masks & mbit) eval_fastmask<KIND>(c, wbase, lane, acc);
-        else eval_slow<KIND>(c, wbase, lane, acc);
+      for (; i + 1 < nf; i += 2) eval_fast2<KIND, PTS>(my[i], my[i + 1], lane_f, acc);
+      if (i < nf) eval_fast<KIND, PTS>(my[i], lane_f, acc);
+      for (int q = SL - 1; q >= SL - no; --q) {
+        const LineC& c = my[q];
+        if (c.masks == 2) eval_fastmask<KIND, PTS>(c, wbase, lane, acc);
+        else eval_slow<KIND, PTS>(c, wbase, lane, acc);
       }
 #pragma unroll
-      for (int k = 0; k < kPts; ++k) sum[k] += acc[k];
-      __syncthreads();
+      for (int k = 0; k < PTS; ++k) sum[k] += acc[k];
+      __syncwarp();
     }
     if (aborted) {
-      if (tid == 0) atomicOr(p.err, ERRB_TIMEOUT);
-      // let copies already in flight land before the CTA leaves (bounded again)
-      for (int b = 0; b < kStages; ++b) mbar_wait_bounded(&bar[b], (phase >> b) & 1u, p.spin_limit);
-      break;
-    }
+      if (lane == 0) { atomicOr(p.err, ERRB_TIMEOUT); abort_sh = 1; }
+    } else {
 #pragma unroll
-    for (int k = 0; k < kPts; ++k) {
-      const int li = wbase + lane + 32 * k;
-      const int64_t i = i0 + li;
-      if (item.slot < 0) {
-        if (i < p.n_grid) {
-          float* o = p.sigma + (int64_t)item.cond * p.n_grid + i;
-          if (p.accumulate) { if (nst) *o += sum[k]; } else *o = sum[k];
+      for (int k = 0; k < PTS; ++k) {
+        const int li = wbase + lane + 32 * k;
+        const int64_t gi = i0 + li;
+        if (item.slot < 0) {
+          if (gi < p.n_grid) {
+            float* o = p.sigma + (int64_t)item.cond * p.n_grid + gi;
+            if (p.accumulate) { if (nst) *o += sum[k]; } else *o = sum[k];
+          }
+        } else {
+          p.partial[(int64_t)item.slot * SEG + li] = sum[k];
         }
-      } else {
-        p.partial[(int64_t)item.slot * kSeg + li] = sum[k];
       }
     }
-    __syncthreads();
+  }
+  // after a timeout, let copies already issued land before the CTA leaves (bounded again)
+  __syncthreads();
+  if (tid == 0 && abort_sh) {
+    for (int b = 0; b < kNB; ++b)
+      if (issued[b] > 0) mbar_wait_bounded(&full[b], (unsigned)((issued[b] - 1) & 1), p.spin_limit);
   }
 }
 
-constexpr size_t kProfileSmem = (size_t)kStages * kStageBytes + (size_t)kStageLines * sizeof(LineC) +
-                               (size_t)kWarps * 2 * kStageLines * sizeof(uint16_t);
+// Compiled tile configurations: {threads, points per lane, lines per stage, min CTAs per SM}.
+// Segment widths 128, 256, 1024 and 2048 points.
+#define PXC_TILES(X) X(0, 32, 4, 64, 32) X(1, 64, 4, 64, 16) X(2, 128, 8, 64, 6) X(3, 128, 16, 128, 4)
 
-template <int KIND>
-static int occupancy_of() {
+int tile_seg(int tile) {
+#define X(i, T, P, S, M) if (tile == i) return T * P;
+  PXC_TILES(X)
+#undef X
+  return 0;
+}
+
+template <int KIND, int T, int P, int S, int M>
+static int occupancy_one() {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_profile<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kProfileSmem);
+    cudaFuncSetAttribute(k_profile<KIND, T, P, S, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)profile_smem<T, S>());
     attr = true;
   }
   int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_profile<KIND>, kThreadsV, kProfileSmem);
-  return n;
-}
-
-int profile_occupancy(int kind) {
-  int n = 0;
-  switch (kind) {
-    case PXC_GAUSS_DOPPLER: n = occupancy_of<PXC_GAUSS_DOPPLER>(); break;
-    case PXC_GAUSS_HWHM: n = occupancy_of<PXC_GAUSS_HWHM>(); break;
-    case PXC_LORENTZ: n = occupancy_of<PXC_LORENTZ>(); break;
-    default: n = occupancy_of<PXC_VOIGT>(); break;
-  }
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_profile<KIND, T, P, S, M>, T, profile_smem<T, S>());
   return n > 0 ? n : 1;
 }
 
-void launch_profile(const ProfP& p, int grid_ctas, cudaStream_t s) {
+template <int KIND>
+static int occupancy_kind(int tile) {
+#define X(i, T, P, S, M) if (tile == i) return occupancy_one<KIND, T, P, S, M>();
+  PXC_TILES(X)
+#undef X
+  return 1;
+}
+
+int profile_occupancy(int kind, int tile) {
+  switch (kind) {
+    case PXC_GAUSS_DOPPLER: return occupancy_kind<PXC_GAUSS_DOPPLER>(tile);
+    case PXC_GAUSS_HWHM: return occupancy_kind<PXC_GAUSS_HWHM>(tile);
+    case PXC_LORENTZ: return occupancy_kind<PXC_LORENTZ>(tile);
+    default: return occupancy_kind<PXC_VOIGT>(tile);
+  }
+}
+
+template <int KIND>
+static void launch_kind(const ProfP& p, int tile, int grid_ctas, cudaStream_t s) {
+#define X(i, T, P, S, M) \
+  if (tile == i) { k_profile<KIND, T, P, S, M><<<grid_ctas, T, profile_smem<T, S>(), s>>>(p); return; }
+  PXC_TILES(X)
+#undef X
+}
+
+void launch_profile(const ProfP& p, int tile, int grid_ctas, cudaStream_t s) {
   switch (p.kind) {
-    case PXC_GAUSS_DOPPLER: k_profile<PXC_GAUSS_DOPPLER><<<grid_ctas, kThreadsV, kProfileSmem, s>>>(p); break;
-    case PXC_GAUSS_HWHM: k_profile<PXC_GAUSS_HWHM><<<grid_ctas, kThreadsV, kProfileSmem, s>>>(p); break;
-    case PXC_LORENTZ: k_profile<PXC_LORENTZ><<<grid_ctas, kThreadsV, kProfileSmem, s>>>(p); break;
-    default: k_profile<PXC_VOIGT><<<grid_ctas, kThreadsV, kProfileSmem, s>>>(p); break;
+    case PXC_GAUSS_DOPPLER: launch_kind<PXC_GAUSS_DOPPLER>(p, tile, grid_ctas, s); break;
+    case PXC_GAUSS_HWHM: launch_kind<PXC_GAUSS_HWHM>(p, tile, grid_ctas, s); break;
+    case PXC_LORENTZ: launch_kind<PXC_LORENTZ>(p, tile, grid_ctas, s); break;
+    default: launch_kind<PXC_VOIGT>(p, tile, grid_ctas, s); break;
   }
   note_launches(1);
 }
-
 
 // ------------------------------------------------------------------ adjoint
 // One warp per sorted line: the lanes stride over the line's window, recompute the

@@ -39,20 +39,27 @@ size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
   size_t err, counters, qpart, qres, slots, cond, srec, sfast, key, Iv, bcount, skey0, skey1, sidx0, sidx1, rcount, pos,
       par, Is, su, sl, sA, sI, segr, seg_items, items, partial, kexp, maxbits, params, total;
-  int64_t max_seg, max_items, max_partial, max_slots, nblk_I, nblk_sort, max_cond, is_stride;
+  int64_t max_seg, max_items, max_slots, nblk_I, nblk_sort, max_cond, is_stride;
+  int64_t partial_floats;  // partial-row buffer; a tile of S points has partial_floats / S rows
 };
+
+// Largest number of partial rows a split single-condition call can need with segments of
+// `seg` points: every line meets at most kWinCap / seg + 2 segments, and items hold at
+// least kItemLines lines unless the row budget allows more splitting.
+int64_t split_rows(int64_t ml, int seg) { return ml * (kWinCap / seg + 2) / kItemLines + 1; }
 
 Layout make_layout(const pxc_capacity& c) {
   Layout L{};
   const int64_t ml = std::max<int64_t>(c.max_lines, 1);
   L.max_cond = std::max<int32_t>(c.max_conditions, 1);
   L.max_slots = c.max_temperatures > 0 ? std::min<int64_t>(c.max_temperatures, L.max_cond) : L.max_cond;
-  L.max_seg = (std::max<int64_t>(c.max_grid, 1) + kSeg - 1) / kSeg;
+  L.max_seg = (std::max<int64_t>(c.max_grid, 1) + kSegMin - 1) / kSegMin;  // narrowest tile: most segments
   L.nblk_I = (ml + kLinesPerBlockI - 1) / kLinesPerBlockI;
   L.nblk_sort = (ml + kSortTile - 1) / kSortTile;
-  const int64_t split = ml * (kWinCap / kSeg + 2) / kItemLines + 1;
-  L.max_partial = split;
-  L.max_items = std::max<int64_t>(L.max_seg + split, L.max_cond * L.max_seg);
+  L.partial_floats = 0;
+  for (int t = 0; t < kNumTiles; ++t)
+    L.partial_floats = std::max<int64_t>(L.partial_floats, split_rows(ml, tile_seg(t)) * tile_seg(t));
+  L.max_items = std::max<int64_t>(L.max_seg + L.partial_floats / kSegMin, L.max_cond * L.max_seg);
   L.is_stride = ((ml + kPad) + 3) & ~(int64_t)3;
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t r = o; o += al(bytes); return r; };
@@ -82,7 +89,7 @@ Layout make_layout(const pxc_capacity& c) {
   L.segr = take((size_t)2 * L.max_seg * 4);
   L.seg_items = take((size_t)(L.max_cond * L.max_seg + 1) * 4);
   L.items = take((size_t)L.max_items * sizeof(Item));
-  L.partial = take((size_t)L.max_partial * kSeg * 4);
+  L.partial = take((size_t)L.partial_floats * 4);
   L.kexp = take((size_t)L.max_slots * 2 * 4);
   L.maxbits = take((size_t)L.max_slots * 8);
   L.params = take(4096);
@@ -117,7 +124,7 @@ pxc_status check_grid(const pxc_grid* g, double cut) {
   if (!g || !(g->dnu > 0.0) || g->n < 1 || !std::isfinite(g->nu_min) || !std::isfinite(g->dnu))
     return fail(PXC_ERR_ARG, "grid: dnu must be > 0 and n >= 1");
   if (!(cut >= 0.0) || !std::isfinite(cut)) return fail(PXC_ERR_ARG, "cutoff must be finite and >= 0");
-  if (g->n > (int64_t)INT32_MAX - 2 * kSeg) return fail(PXC_ERR_ARG, "grid: too many points");
+  if (g->n > (int64_t)INT32_MAX - 2 * kSegMax) return fail(PXC_ERR_ARG, "grid: too many points");
   return PXC_OK;
 }
 
@@ -170,9 +177,11 @@ struct WsExtra {
   unsigned long long* h_cnt;
   cudaStream_t copy_stream;
   cudaEvent_t ev_copied[2], ev_done[2];
-  int occ[4];
+  int occ[4][kNumTiles];  // resident profile CTAs per SM for each kind and tile
+  int tile[4][2];         // tile used for each kind, [single condition, batched]
   // last call
   int64_t last_nseg;
+  int last_seg, last_tile;
   int64_t last_nkept_max;
   // optional CUDA-event timing of the passes: [0] intensity, [1] compaction+sort+prepare, [2] profile
   int timing;
@@ -312,9 +321,9 @@ void tmark(pxc_workspace* ws, int pass, bool start, cudaStream_t s) {
   ++x->ev_next;
 }
 
-int profile_ctas(pxc_workspace* ws, int kind) {
+int profile_ctas(pxc_workspace* ws, int kind, int tile) {
   WsExtra* x = X(ws);
-  int occ = x->occ[kind] > 0 ? x->occ[kind] : 1;
+  int occ = x->occ[kind][tile] > 0 ? x->occ[kind][tile] : 1;
   return ws->sm_count * occ;
 }
 
@@ -366,7 +375,13 @@ pxc_status pxc_workspace_create(const pxc_capacity* cap, void* scratch, size_t b
     cudaEventCreateWithFlags(&x->ev_copied[i], cudaEventDisableTiming);
     cudaEventCreateWithFlags(&x->ev_done[i], cudaEventDisableTiming);
   }
-  for (int k = 0; k < 4; ++k) x->occ[k] = profile_occupancy(k);
+  for (int k = 0; k < 4; ++k) {
+    for (int t = 0; t < kNumTiles; ++t) x->occ[k][t] = profile_occupancy(k, t);
+    // defaults: narrow segments balance dense single-condition spectra best; batched
+    // tables (most lines zero in most conditions) pay less staging with wide segments
+    x->tile[k][0] = 0;
+    x->tile[k][1] = kNumTiles - 1;
+  }
   cudaMemset(ws->err, 0, 256);
   cudaMemset(ws->counters, 0, CNT_N * 8);
   cudaDeviceSynchronize();
@@ -491,11 +506,14 @@ pxc_status pxc_cross_section(pxc_workspace* ws, const pxc_states* st, const pxc_
     return fail(PXC_ERR_CAPACITY, "cross_section: above workspace capacity");
   if (ws->accumulate && n_c != 1) return fail(PXC_ERR_ARG, "accumulate mode needs n_c == 1");
   const double wpts = 2.0 * pa->cutoff / grid->dnu + 2.0;
-  const int64_t nseg = (grid->n + kSeg - 1) / kSeg;
+  const int tile = x->tile[pa->kind][n_c > 1 ? 1 : 0];
+  const int seg = tile_seg(tile);
+  const int64_t nseg = (grid->n + seg - 1) / seg;
+  const int64_t max_partial = L.partial_floats / seg;
   if (n_c == 1 && wpts > kWinCap) {
     // the split-item table is sized for windows up to kWinCap points
-    const int64_t need = nseg + (int64_t)((double)tr->n * (wpts / kSeg + 2.0) / kItemLines) + 1;
-    if (need > L.max_items || need - nseg > L.max_partial)
+    const int64_t need = nseg + (int64_t)((double)tr->n * (wpts / seg + 2.0) / kItemLines) + 1;
+    if (need > L.max_items || need - nseg > max_partial)
       return fail(PXC_ERR_CAPACITY, "cross_section: cut-off window too wide for this workspace");
   }
   GridP gp = make_gridp(*grid, pa->cutoff);
@@ -551,10 +569,10 @@ pxc_status pxc_cross_section(pxc_workspace* ws, const pxc_states* st, const pxc_
     for (int i = 0; i < n_c; ++i)
       cudaMemcpyAsync(sigma_exp_out + i, kexp + 2 * slot_of[i], 4, cudaMemcpyDeviceToDevice, s);
   }
-  launch_segments(at<int4>(ws, L.pos), cnt + CNT_KEPT, nseg, at<int32_t>(ws, L.segr), s);
+  const int ctas = profile_ctas(ws, pa->kind, tile);
+  launch_segments(at<int4>(ws, L.pos), cnt + CNT_KEPT, nseg, seg, at<int32_t>(ws, L.segr), s);
   launch_items(at<int32_t>(ws, L.segr), nseg, n_c, n_c == 1 ? kItemLines : INT32_MAX / 2, at<int32_t>(ws, L.seg_items),
-               at<Item>(ws, L.items), cnt, L.max_items, n_c == 1 ? 16ll * profile_ctas(ws, pa->kind) : 0ll,
-               L.max_partial, s);
+               at<Item>(ws, L.items), cnt, L.max_items, n_c == 1 ? 16ll * ctas : 0ll, max_partial, s);
   ProfP p{};
   p.pos = at<int4>(ws, L.pos);
   p.par = at<float2>(ws, L.par);
@@ -574,12 +592,14 @@ pxc_status pxc_cross_section(pxc_workspace* ws, const pxc_states* st, const pxc_
   p.err = ws->err;
   p.spin_limit = 4000000000ll;  // ~2 s of clock cycles
   tmark(ws, 2, true, s);
-  launch_profile(p, profile_ctas(ws, pa->kind), s);
+  launch_profile(p, tile, ctas, s);
   tmark(ws, 2, false, s);
   if (n_c == 1)
-    launch_reduce_partials(at<Item>(ws, L.items), at<int32_t>(ws, L.seg_items), nseg, 1, at<float>(ws, L.partial),
-                           sigma_out, grid->n, s);
+    launch_reduce_partials(at<Item>(ws, L.items), at<int32_t>(ws, L.seg_items), nseg, seg, 1,
+                           at<float>(ws, L.partial), sigma_out, grid->n, s);
   x->last_nseg = nseg;
+  x->last_seg = seg;
+  x->last_tile = tile;
   ws->last_nc = n_c;
   return cuda_check("cross_section");
 }
@@ -638,7 +658,7 @@ pxc_status pxc_cross_section_backward(pxc_workspace* ws, const pxc_states* st, c
   p.lineP = at<double>(ws, L.sI);
   launch_adjoint(p, s);
   launch_adjoint_reduce(p.lineT, p.lineTv, p.lineP, cnt + CNT_KEPT, tr->n, dL_dT, dL_dTvib, dL_dP, s);
-  x->last_nseg = (grid->n + kSeg - 1) / kSeg;
+  x->last_nseg = 0;  // the adjoint does not bin lines into segments
   ws->last_nc = 1;
   return cuda_check("cross_section_backward");
 }
@@ -655,10 +675,70 @@ pxc_status pxc_get_stats(pxc_workspace* ws, cudaStream_t s, pxc_stats* out) {
   out->n_nonzero = (int64_t)x->h_cnt[CNT_NONZERO];
   out->evals_window = (int64_t)x->h_cnt[CNT_EVALS];
   out->evals_nonzero = (int64_t)x->h_cnt[CNT_EVALS_NZ];
-  out->segment_points = kSeg;
+  out->segment_points = x->last_seg;
   out->n_segments = (int32_t)x->last_nseg;
   out->I_exp = k;
-  out->reserved = 0;
+  out->tile = x->last_tile;
+  return r;
+}
+
+pxc_status pxc_set_tile(pxc_workspace* ws, int32_t kind, int32_t batched, int32_t tile) {
+  if (!ws || kind < 0 || kind > 3 || batched < 0 || batched > 1 || tile < 0 || tile >= kNumTiles)
+    return fail(PXC_ERR_ARG, "set_tile: bad arguments");
+  X(ws)->tile[kind][batched] = tile;
+  return PXC_OK;
+}
+
+pxc_status pxc_get_tile(pxc_workspace* ws, int32_t kind, int32_t batched, int32_t* tile) {
+  if (!ws || !tile || kind < 0 || kind > 3 || batched < 0 || batched > 1)
+    return fail(PXC_ERR_ARG, "get_tile: bad arguments");
+  *tile = X(ws)->tile[kind][batched];
+  return PXC_OK;
+}
+
+pxc_status pxc_autotune(pxc_workspace* ws, const pxc_states* st, const pxc_transitions* tr, const pxc_condition* c,
+                        int32_t n_c, const pxc_grid* grid, const pxc_profile_args* pa, double threshold,
+                        float* sigma_out, int32_t* sigma_exp_out, int32_t repeats, int32_t* tile_out,
+                        double* ms_out, cudaStream_t s) {
+  if (!ws || !pa || pa->kind < 0 || pa->kind > 3 || n_c < 1 || repeats < 1)
+    return fail(PXC_ERR_ARG, "autotune: bad arguments");
+  if (ws->accumulate) return fail(PXC_ERR_ARG, "autotune: not in accumulate mode (runs the call repeatedly)");
+  WsExtra* x = X(ws);
+  const int b = n_c > 1 ? 1 : 0;
+  const int saved = x->tile[pa->kind][b];
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best_ms = 0.0;
+  int best = -1;
+  pxc_status r = PXC_OK;
+  for (int t = 0; t < kNumTiles && !r; ++t) {
+    x->tile[pa->kind][b] = t;
+    r = pxc_cross_section(ws, st, tr, c, n_c, grid, pa, threshold, sigma_out, sigma_exp_out, s);
+    if (r) break;
+    cudaEventRecord(e0, s);
+    for (int i = 0; i < repeats && !r; ++i)
+      r = pxc_cross_section(ws, st, tr, c, n_c, grid, pa, threshold, sigma_out, sigma_exp_out, s);
+    cudaEventRecord(e1, s);
+    if (r) break;
+    if ((r = pxc_sync_status(ws, s))) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double per = (double)ms / repeats;
+    if (ms_out) ms_out[t] = per;
+    if (best < 0 || per < best_ms) { best_ms = per; best = t; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (r || best < 0) {
+    x->tile[pa->kind][b] = saved;
+    return r ? r : fail(PXC_ERR_ARG, "autotune: nothing timed");
+  }
+  x->tile[pa->kind][b] = best;
+  if (tile_out) *tile_out = best;
+  // leave the chosen tile's result in the outputs
+  if (best != kNumTiles - 1) r = pxc_cross_section(ws, st, tr, c, n_c, grid, pa, threshold, sigma_out, sigma_exp_out, s);
+  if (!r) r = pxc_sync_status(ws, s);
   return r;
 }
 

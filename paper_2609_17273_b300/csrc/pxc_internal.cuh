@@ -39,10 +39,11 @@ constexpr int kSortItems = kSortTile / kSortThreads;
 constexpr int kQBlocks = 1184;            // 148 SMs x 8, fixed so the Q reduction order is fixed
 constexpr int kThreadsQ = 256;
 
-// Profile kernel: segment of S = kThreadsV * kPts grid points per work item.
-constexpr int kThreadsV = 128;
-constexpr int kPts = 16;
-constexpr int kSeg = kThreadsV * kPts;    // 2048
+// Profile kernel tiles: segment widths are a runtime choice among the compiled configurations
+// (see kernels_profile.cu); the workspace is sized for the narrowest and the widest.
+constexpr int kNumTiles = 4;
+constexpr int kSegMin = 128;
+constexpr int kSegMax = 2048;
 constexpr int kStageLines = 256;          // lines per TMA stage (two per thread for the constants)
 constexpr int kStages = 2;
 constexpr int kItemLines = 32768;         // a segment with more lines is split into several items
@@ -109,11 +110,11 @@ struct pxc_workspace {
   int32_t* segr;                 // [2][max_seg]
   pxc::Item* items;              // [max_items]
   int32_t* seg_items;            // [max_cond * max_seg + 1] exclusive prefix of items
-  float* partial;                // [max_partial][kSeg]
+  float* partial;                // partial rows of the segment width in use
   pxc::CondDev* cond;            // [max_cond]
   int32_t* kexp;                 // [max_slots] exponent per slot
   unsigned long long* maxbits;   // [max_slots]
-  int64_t max_seg, max_items, max_partial, max_slots, nblk_I, nblk_sort;
+  int64_t max_seg, max_items, max_slots, nblk_I, nblk_sort;
   // host mirror of the last call
   int64_t last_nseg;
   int32_t last_nc;
