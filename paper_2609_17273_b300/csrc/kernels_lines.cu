@@ -143,6 +143,94 @@ void launch_boltzmann(const pxc_states* st, const SlotP* slots_dev, int nslot, d
   note_launches(2);
 }
 
+// ------------------------------------------------------------------ per-state energy codes
+// Ordered 64-bit key of a double (monotone in the value for non-NaN inputs).
+__device__ __forceinline__ unsigned long long dkey(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double dkey_inv(unsigned long long k) {
+  const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+  return __longlong_as_double((long long)b);
+}
+
+// words[0] = max key(-E), words[1] = max key(E) over finite E (0: none), words[2] = max g.
+__global__ void __launch_bounds__(256) k_state_range(const double* __restrict__ E, const int32_t* __restrict__ g,
+                                                     int64_t n, unsigned long long* __restrict__ words) {
+  unsigned long long kmin = 0, kmax = 0, gm = 0;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+    const double e = E[s];
+    if (isfinite(e)) {
+      const unsigned long long a = dkey(-e), b = dkey(e);
+      kmin = a > kmin ? a : kmin;
+      kmax = b > kmax ? b : kmax;
+    }
+    const int32_t gv = g[s];
+    const unsigned long long gg = gv > 0 ? (unsigned long long)gv : 0ull;
+    gm = gg > gm ? gg : gm;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long v = __shfl_down_sync(0xffffffffu, kmin, o);
+    kmin = v > kmin ? v : kmin;
+    v = __shfl_down_sync(0xffffffffu, kmax, o);
+    kmax = v > kmax ? v : kmax;
+    v = __shfl_down_sync(0xffffffffu, gm, o);
+    gm = v > gm ? v : gm;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (kmin) atomicMax(&words[0], kmin);
+    if (kmax) atomicMax(&words[1], kmax);
+    if (gm) atomicMax(&words[2], gm);
+  }
+}
+
+__device__ __forceinline__ QuantHdr quant_header(const unsigned long long* words) {
+  QuantHdr h{};
+  const unsigned long long kmin = words[0], kmax = words[1];
+  const double gmax = (double)(words[2] > 0 ? words[2] : 1ull);
+  h.log2_gmax = (float)(log2(gmax) + 1e-6);
+  if (!kmin || !kmax) return h;  // no finite energy
+  const double emin = -dkey_inv(kmin), emax = dkey_inv(kmax);
+  const double span = emax - emin;
+  const double inv = span > 0.0 ? (double)(kCodeMax - 2) / span : 1.0;
+  if (!isfinite(span) || !(inv > 0.0) || !isfinite(inv)) return h;
+  h.Emin = emin;
+  h.inv_res = inv;
+  h.res_f = __double2float_ru(__ddiv_ru(1.0, inv));
+  h.Emin_f = __double2float_rd(emin);
+  h.enabled = isfinite(h.res_f) && h.res_f > 0.f && isfinite(h.Emin_f);
+  return h;
+}
+
+__global__ void __launch_bounds__(256) k_state_quant(const double* __restrict__ E, int64_t n,
+                                                     const unsigned long long* __restrict__ words,
+                                                     code_t* __restrict__ code, QuantHdr* __restrict__ hdr) {
+  const QuantHdr h = quant_header(words);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *hdr = h;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+    const double e = E[s];
+    int q = kCodeNone;
+    if (h.enabled && isfinite(e)) {
+      const double x = floor((e - h.Emin) * h.inv_res);
+      q = x < 0.0 ? 0 : (x > (double)kCodeMax ? kCodeMax : (int)x);
+    }
+    code[s] = (code_t)q;
+  }
+}
+
+void launch_state_codes(const pxc_states* st, code_t* code, unsigned long long* words, cudaStream_t s) {
+  cudaMemsetAsync(words, 0, 3 * sizeof(unsigned long long), s);
+  const int64_t n = st->n;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 148 * 8) blocks = 148 * 8;
+  if (blocks < 1) blocks = 1;
+  QuantHdr* hdr = reinterpret_cast<QuantHdr*>(words + kQuantWords);
+  k_state_range<<<(unsigned)blocks, 256, 0, s>>>(st->E, st->g, n, words);
+  k_state_quant<<<(unsigned)blocks, 256, 0, s>>>(st->E, n, words, code, hdr);
+  note_launches(2);
+}
+
 // ------------------------------------------------------------------ K-I: intensities
 // nu = E[u] - E[l] (FP64), keep = nu > 0 and window meets the grid and I >= threshold;
 // I = g_u A (b_l - b_u) / (8 pi c nu^2 Q), the Boltzmann factors from the per-state table
@@ -237,6 +325,12 @@ void launch_lines(const pxc_transitions* tr, const int32_t* g, int64_t ns, const
 // table or dividing: |I| <= g_u A max(b_l, b_u) m / (8 pi c Q nu^2), m = min(1, c2 nu/T) for
 // LTE (b_l - b_u = b_l (1 - e^{-c2 nu/T})) and m = 1 for two temperatures, evaluated in log2
 // units with a 1e-3 margin that covers every FP32 rounding in it.
+//
+// Before any 16-byte state record is read, a prefilter on the 16-bit state codes (a table of
+// 2 bytes per state, small enough to stay in L2 for 5e7 states) rejects lines whose nu is
+// certainly outside the kept window, and, for LTE with a threshold, lines whose intensity is
+// certainly below it: nu_lo = (d - 3) res, nu_hi = (d + 3) res with d = q_u - q_l, b_l <=
+// exp(-c2 E_lo(q_l) / T), g_u <= max g.  Only the surviving candidates gather their states.
 
 
 // Block-wide exclusive rank of `flag` among the 256 threads in thread order, and the total.
@@ -253,99 +347,206 @@ __device__ __forceinline__ uint32_t block_rank(bool flag, uint32_t* wsum, uint32
   return before + __popc(m & ((1u << lane) - 1u));
 }
 
+// Code load kept in L2 with the evict-last policy (the state codes are re-read at random).
+__device__ __forceinline__ int ld_code(const code_t* p, uint64_t pol) {
+  unsigned short v;
+  asm volatile("ld.global.nc.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(pol));
+  return (int)v;
+}
+
+// Per-block constants of the compacting intensity pass (computed once per CTA by one thread).
+struct LinesConst {
+  double invQ;
+  float l2invQ, lo_scale, hi_scale, Emin_f, log2_gmax;
+  int dlo, dhi, pre, pre_thr;
+};
+
+// One warp owns a unit of kUnitLines consecutive lines and walks it 32 lines at a time; its
+// candidates queue (in line order) in a per-warp buffer that is drained 32 at a time, so the
+// state gathers and the FP64 test run on full warps and no CTA barrier is needed per round.
+// Kept lines go to the unit's own staging range in line order, counted per unit.
+constexpr int kCandBuf = 64;
+
 __global__ void __launch_bounds__(kThreadsI) k_lines_c(const int32_t* __restrict__ up, const int32_t* __restrict__ lo,
                                                        const void* __restrict__ Av, int A32, int64_t n,
+                                                       const code_t* __restrict__ code,
+                                                       const QuantHdr* __restrict__ qhp,
                                                        const StateFast* __restrict__ sfast,
                                                        const double2* __restrict__ srec, int64_t ns,
                                                        const double* __restrict__ qres, GridP gp, double threshold,
                                                        BoundP bp, int with_I, uint64_t* __restrict__ kstage,
                                                        uint32_t* __restrict__ istage, double* __restrict__ Iv,
-                                                       uint32_t* __restrict__ bcount,
+                                                       uint32_t* __restrict__ ucount, int64_t nunit,
                                                        unsigned long long* __restrict__ maxbits, unsigned* err) {
-  __shared__ uint32_t wsum[kThreadsI / 32];
-  // candidates of one round for the exact FP64 test, packed so the FP64 work runs on dense warps
-  __shared__ uint32_t c_t[kThreadsI];
-  __shared__ int32_t c_u[kThreadsI], c_l[kThreadsI], c_g[kThreadsI];
-  __shared__ double c_nu[kThreadsI], c_A[kThreadsI];
-  const double invQ = with_I ? qres[3] : 0.0;
-  const float l2invQ = with_I ? (float)log2(invQ) : 0.f;
-  const int64_t base = (int64_t)blockIdx.x * kLinesPerBlockI;
+  constexpr int NW = kThreadsI / 32;
+  __shared__ LinesConst kc;
+  __shared__ uint32_t cb_t[NW][kCandBuf];
+  __shared__ int32_t cb_u[NW][kCandBuf], cb_l[NW][kCandBuf];
+  __shared__ unsigned long long cb_A[NW][kCandBuf];  // A: FP32 bits (A32) or FP64 bits
+  __shared__ unsigned long long wmax[NW];
+  if (threadIdx.x == 0) {
+    LinesConst c{};
+    c.invQ = with_I ? qres[3] : 0.0;
+    c.l2invQ = with_I ? (float)log2(c.invQ) : 0.f;
+    QuantHdr qh{};
+    if (code) qh = *qhp;
+    const double nu_max = gp.nu_min + (double)(gp.n - 1) * gp.dnu;
+    const double wl = gp.exact_bounds ? gp.nu_keep_lo : fmax(gp.nu_min - gp.cut, 0.0);
+    const double wh = gp.exact_bounds ? gp.nu_keep_hi : nu_max + gp.cut;
+    // the codes are used when their resolution is at most 1/16 of the kept nu range (a list
+    // whose energies span far more than the window gains nothing from them)
+    c.pre = code != nullptr && qh.enabled && (wh - wl) * qh.inv_res >= 16.0;
+    c.pre_thr = c.pre && with_I && threshold > 0.0 && bp.lte;
+    c.dlo = INT_MIN;
+    c.dhi = INT_MAX;
+    if (c.pre) {
+      // kept lines have nu in [wl, wh] (infinite ends: none kept); widen by two grid steps,
+      // a relative 1e-9 and four code steps
+      const double a = isinf(wl) ? (wl > 0 ? 2e9 : -2e9)
+                                 : floor((wl - 2.0 * gp.dnu - 1e-9 * fabs(wl)) * qh.inv_res) - 4.0;
+      const double b = isinf(wh) ? (wh > 0 ? 2e9 : -2e9)
+                                 : ceil((wh + 2.0 * gp.dnu + 1e-9 * fabs(wh)) * qh.inv_res) + 4.0;
+      c.dlo = a < -1e9 ? -1000000000 : (a > 1e9 ? 1000000000 : (int)a);
+      c.dhi = b > 1e9 ? 1000000000 : (b < -1e9 ? -1000000000 : (int)b);
+    }
+    c.lo_scale = qh.res_f * 0.99999f;
+    c.hi_scale = qh.res_f * 1.00001f;
+    c.Emin_f = qh.Emin_f;
+    c.log2_gmax = qh.log2_gmax;
+    kc = c;
+  }
+  __syncthreads();
+  const LinesConst c = kc;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t unit = (int64_t)blockIdx.x * NW + warp;
   const long long lo_bits = __double_as_longlong(gp.nu_keep_lo), hi_bits = __double_as_longlong(gp.nu_keep_hi);
-  const int lane = threadIdx.x & 31;
-  uint32_t run = 0;
+  const float kl2e = 1.4426950408889634f;
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
   unsigned long long mx = 0;
   unsigned bad = 0;
-  for (int k = 0; k < kLinesPerBlockI / kThreadsI; ++k) {
-    const int64_t t = base + k * kThreadsI + threadIdx.x;
+  uint32_t run = 0;  // kept lines of this unit so far
+  int nb = 0;        // queued candidates
+  const int64_t ubase = unit * kUnitLines;
+
+  // Exact selection of the first `cnt` queued candidates (lane i takes entry i), in queue order.
+  auto drain = [&](int cnt) {
     bool keep = false;
-    double nu = 0.0, A = 0.0;
-    int32_t u = 0, l = 0, g = 0;
-    if (t < n) {
-      u = up[t];
-      l = lo[t];
-      A = A32 ? (double)((const float*)Av)[t] : ((const double*)Av)[t];
-      if (u < 0 || u >= ns || l < 0 || l >= ns) {
-        bad |= ERRB_ID;
+    double nu = 0.0, I = 0.0;
+    uint32_t t = 0;
+    if (lane < cnt) {
+      t = cb_t[warp][lane];
+      const int32_t u = cb_u[warp][lane], l = cb_l[warp][lane];
+      const unsigned long long ab = cb_A[warp][lane];
+      const double A = A32 ? (double)__uint_as_float((unsigned)ab) : __longlong_as_double((long long)ab);
+      const StateFast fu = sfast[u], fl = sfast[l];
+      nu = __dsub_rn(fu.E, fl.E);
+      if (gp.exact_bounds) {
+        const long long nbits = __double_as_longlong(nu);
+        keep = nbits >= lo_bits && nbits <= hi_bits;
       } else {
-        if (!isfinite(A)) bad |= ERRB_NONFINITE;
-        const StateFast fu = sfast[u], fl = sfast[l];
-        g = fu.g;
-        nu = __dsub_rn(fu.E, fl.E);
-        if (gp.exact_bounds) {
-          const long long nb = __double_as_longlong(nu);
-          keep = nb >= lo_bits && nb <= hi_bits;
-        } else {
-          int64_t a, b;
-          keep = nu > 0.0 && exact_window(nu, gp, &a, &b);
-        }
-        if (keep && with_I && threshold > 0.0) {
+        int64_t a, b;
+        keep = nu > 0.0 && exact_window(nu, gp, &a, &b);
+      }
+      if (keep && with_I) {
+        if (threshold > 0.0) {
           const float nuf = (float)nu;
           const float m = bp.lte ? fminf(1.f, bp.c2_T * nuf) : 1.f;
-          const float P = (float)g * (float)A * m / (nuf * nuf);
-          if (__log2f(P) + fmaxf(fu.lb, fl.lb) + l2invQ < bp.log2_thr) keep = false;
+          const float P = (float)fu.g * (float)A * m / (nuf * nuf);
+          if (__log2f(P) + fmaxf(fu.lb, fl.lb) + c.l2invQ < bp.log2_thr) keep = false;
+        }
+        if (keep) {
+          const double num = (double)fu.g * A * c.invQ * (srec[l].y - srec[u].y);
+          const double den = nu * nu;
+          keep = fabs(num) >= threshold * den;
+          if (keep) I = num / den;
         }
       }
     }
-    uint32_t tot;
-    if (!with_I) {
-      const uint32_t r = block_rank(keep, wsum, &tot);
-      if (keep) {
-        kstage[base + run + r] = (uint64_t)__double_as_longlong(nu);
-        istage[base + run + r] = (uint32_t)t;
-      }
-      run += tot;
-      continue;
-    }
-    // pack the candidates of this round (index order) ...
-    const uint32_t r = block_rank(keep, wsum, &tot);
+    const unsigned kb = __ballot_sync(0xffffffffu, keep);
     if (keep) {
-      c_t[r] = (uint32_t)t; c_u[r] = u; c_l[r] = l; c_g[r] = g; c_nu[r] = nu; c_A[r] = A;
+      const int64_t o = ubase + run + __popc(kb & lt);
+      kstage[o] = (uint64_t)__double_as_longlong(nu);
+      istage[o] = t;
+      if (with_I) {
+        Iv[t] = I;
+        const unsigned long long ib = (unsigned long long)__double_as_longlong(fabs(I));
+        mx = ib > mx ? ib : mx;
+      }
     }
-    __syncthreads();
-    // ... and run the exact test on the first `tot` threads
-    bool kept = false;
-    double I = 0.0;
-    uint32_t tt = 0;
-    if (threadIdx.x < tot) {
-      tt = c_t[threadIdx.x];
-      const double nuc = c_nu[threadIdx.x];
-      const double num = (double)c_g[threadIdx.x] * c_A[threadIdx.x] * invQ *
-                         (srec[c_l[threadIdx.x]].y - srec[c_u[threadIdx.x]].y);
-      const double den = nuc * nuc;
-      kept = fabs(num) >= threshold * den;
-      if (kept) I = num / den;
-      nu = nuc;
+    run += __popc(kb);
+  };
+
+  if (unit < nunit) {
+    for (int r = 0; r < kUnitLines / 32; ++r) {
+      const int64_t t = ubase + r * 32 + lane;
+      bool cand = false;
+      int32_t u = 0, l = 0;
+      unsigned long long ab = 0;
+      if (t < n) {
+        u = __ldcs(up + t);
+        l = __ldcs(lo + t);
+        float Af;
+        bool finite;
+        if (A32) {
+          Af = __ldcs((const float*)Av + t);
+          ab = __float_as_uint(Af);
+          finite = (ab & 0x7f800000u) != 0x7f800000u;
+        } else {
+          const double A = __ldcs((const double*)Av + t);
+          ab = (unsigned long long)__double_as_longlong(A);
+          finite = (ab & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
+          Af = (float)A;
+        }
+        if (u < 0 || u >= ns || l < 0 || l >= ns) {
+          bad |= ERRB_ID;
+        } else {
+          if (!finite) bad |= ERRB_NONFINITE;
+          cand = true;
+          if (c.pre) {
+            const int qu = ld_code(code + u, pol), ql = ld_code(code + l, pol);
+            if (qu != kCodeNone && ql != kCodeNone) {
+              const int d = qu - ql;
+              if (d < c.dlo || d > c.dhi) {
+                cand = false;
+              } else if (c.pre_thr && d > 3) {
+                const float nul = (float)(d - 3) * c.lo_scale, nuh = (float)(d + 3) * c.hi_scale;
+                const float m = fminf(1.f, bp.c2_T * nuh);
+                const float Elo = fmaf((float)(ql - 1), ql >= 1 ? c.lo_scale : c.hi_scale, c.Emin_f);
+                const float lbl = -(bp.c2_T * kl2e) * Elo;  // log2 of the upper bound of b_l
+                const float Pb = Af * m / (nul * nul);
+                if (__log2f(Pb) + c.log2_gmax + lbl + c.l2invQ < bp.log2_thr - 1e-6f * fabsf(lbl)) cand = false;
+              }
+            }
+          }
+        }
+      }
+      const unsigned cm = __ballot_sync(0xffffffffu, cand);
+      if (cand) {
+        const int p = nb + __popc(cm & lt);
+        cb_t[warp][p] = (uint32_t)t;
+        cb_u[warp][p] = u;
+        cb_l[warp][p] = l;
+        cb_A[warp][p] = ab;
+      }
+      nb += __popc(cm);
+      __syncwarp();
+      if (nb >= 32) {
+        drain(32);
+        __syncwarp();
+        if (lane < nb - 32) {
+          cb_t[warp][lane] = cb_t[warp][lane + 32];
+          cb_u[warp][lane] = cb_u[warp][lane + 32];
+          cb_l[warp][lane] = cb_l[warp][lane + 32];
+          cb_A[warp][lane] = cb_A[warp][lane + 32];
+        }
+        nb -= 32;
+        __syncwarp();
+      }
     }
-    uint32_t tot2;
-    const uint32_t r2 = block_rank(kept, wsum, &tot2);
-    if (kept) {
-      kstage[base + run + r2] = (uint64_t)__double_as_longlong(nu);
-      istage[base + run + r2] = tt;
-      Iv[tt] = I;
-      const unsigned long long ib = (unsigned long long)__double_as_longlong(fabs(I));
-      mx = ib > mx ? ib : mx;
-    }
-    run += tot2;
+    if (nb > 0) drain(nb);
+    if (lane == 0) ucount[unit] = run;
   }
   if (bad) set_err(err, bad);
   if (with_I) {
@@ -354,40 +555,49 @@ __global__ void __launch_bounds__(kThreadsI) k_lines_c(const int32_t* __restrict
       const unsigned long long v = __shfl_down_sync(0xffffffffu, mx, o);
       mx = v > mx ? v : mx;
     }
-    if (lane == 0 && mx) atomicMax(maxbits, mx);
+    if (lane == 0) wmax[warp] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long m = 0;
+      for (int i = 0; i < NW; ++i) m = wmax[i] > m ? wmax[i] : m;
+      if (m) atomicMax(maxbits, m);
+    }
   }
-  if (threadIdx.x == 0) bcount[blockIdx.x] = run;
 }
 
-void launch_lines_compact(const pxc_transitions* tr, int64_t ns, const StateFast* sfast, const double2* srec,
+void launch_lines_compact(const pxc_transitions* tr, int64_t ns, const code_t* code, const QuantHdr* qh,
+                          const StateFast* sfast, const double2* srec,
                           const double* qres, const GridP& gp, double threshold, const BoundP& bp, int with_I,
-                          uint64_t* kstage, uint32_t* istage, double* Iv, uint32_t* bcount, int64_t nblk,
+                          uint64_t* kstage, uint32_t* istage, double* Iv, uint32_t* ucount, int64_t nunit,
                           unsigned long long* maxbits, unsigned* err, cudaStream_t s) {
-  if (nblk == 0) return;
-  k_lines_c<<<(unsigned)nblk, kThreadsI, 0, s>>>(tr->upper, tr->lower, tr->A, tr->A_is_f32, tr->n, sfast, srec, ns,
-                                                 qres, gp, threshold, bp, with_I, kstage, istage, Iv, bcount,
-                                                 maxbits, err);
+  if (nunit == 0) return;
+  const int64_t nblk = (nunit + kThreadsI / 32 - 1) / (kThreadsI / 32);
+  k_lines_c<<<(unsigned)nblk, kThreadsI, 0, s>>>(tr->upper, tr->lower, tr->A, tr->A_is_f32, tr->n, code, qh, sfast,
+                                                 srec, ns, qres, gp, threshold, bp, with_I, kstage, istage, Iv,
+                                                 ucount, nunit, maxbits, err);
   note_launches(1);
 }
 
-// Copies each block's staged kept lines to its offset (exclusive scan of the counts, total at [nblk]).
+// Copies each unit's staged kept lines to its offset (exclusive scan of the counts, total at
+// [nunit]); one warp per unit.
 __global__ void __launch_bounds__(256) k_compact_staged(const uint64_t* __restrict__ kstage,
                                                         const uint32_t* __restrict__ istage,
-                                                        const uint32_t* __restrict__ boff, uint64_t* __restrict__ okey,
-                                                        uint32_t* __restrict__ oidx) {
-  const int64_t b = blockIdx.x;
-  const uint32_t off = boff[b], cnt = boff[b + 1] - off;
-  const int64_t base = b * kLinesPerBlockI;
-  for (uint32_t r = threadIdx.x; r < cnt; r += blockDim.x) {
+                                                        const uint32_t* __restrict__ uoff, int64_t nunit,
+                                                        uint64_t* __restrict__ okey, uint32_t* __restrict__ oidx) {
+  const int64_t u = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (u >= nunit) return;
+  const uint32_t off = uoff[u], cnt = uoff[u + 1] - off;
+  const int64_t base = u * kUnitLines;
+  for (uint32_t r = threadIdx.x & 31; r < cnt; r += 32) {
     okey[off + r] = kstage[base + r];
     oidx[off + r] = istage[base + r];
   }
 }
 
-void launch_compact_staged(const uint64_t* kstage, const uint32_t* istage, const uint32_t* boff, int64_t nblk,
+void launch_compact_staged(const uint64_t* kstage, const uint32_t* istage, const uint32_t* uoff, int64_t nunit,
                            uint64_t* okey, uint32_t* oidx, cudaStream_t s) {
-  if (nblk == 0) return;
-  k_compact_staged<<<(unsigned)nblk, 256, 0, s>>>(kstage, istage, boff, okey, oidx);
+  if (nunit == 0) return;
+  k_compact_staged<<<(unsigned)((nunit + 7) / 8), 256, 0, s>>>(kstage, istage, uoff, nunit, okey, oidx);
   note_launches(1);
 }
 

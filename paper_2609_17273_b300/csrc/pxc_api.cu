@@ -38,7 +38,7 @@ size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
   size_t err, counters, qpart, qres, slots, cond, srec, sfast, key, Iv, bcount, skey0, skey1, sidx0, sidx1, rcount, pos,
-      par, Is, su, sl, sA, sI, segr, seg_items, items, partial, kexp, maxbits, params, total;
+      par, Is, su, sl, sA, sI, segr, seg_items, items, partial, kexp, maxbits, params, code, qwords, total;
   int64_t max_seg, max_items, max_slots, nblk_I, nblk_sort, max_cond, is_stride;
   int64_t partial_floats;  // partial-row buffer; a tile of S points has partial_floats / S rows
 };
@@ -73,7 +73,7 @@ Layout make_layout(const pxc_capacity& c) {
   L.sfast = take((size_t)std::max<int64_t>(c.max_states, 1) * sizeof(StateFast));
   L.key = take((size_t)ml * 8);
   L.Iv = take((size_t)ml * 8);
-  L.bcount = take((size_t)(L.nblk_I + 1) * 4);
+  L.bcount = take((size_t)((ml + kUnitLines - 1) / kUnitLines + 1) * 4);  // per unit (>= per block)
   L.skey0 = take((size_t)ml * 8);
   L.skey1 = take((size_t)ml * 8);
   L.sidx0 = take((size_t)ml * 4);
@@ -93,6 +93,8 @@ Layout make_layout(const pxc_capacity& c) {
   L.kexp = take((size_t)L.max_slots * 2 * 4);
   L.maxbits = take((size_t)L.max_slots * 8);
   L.params = take(4096);
+  L.code = take((size_t)std::max<int64_t>(c.max_states, 1) * sizeof(code_t));
+  L.qwords = take(kQuantWords * 8 + sizeof(QuantHdr));
   L.total = o;
   return L;
 }
@@ -265,8 +267,14 @@ void run_boltzmann(pxc_workspace* ws, const pxc_states* st, const pxc_condition&
   upload(ws, dslot, &sp, sizeof sp, s);
   launch_boltzmann(st, dslot, 1, at<double2>(ws, x->L.srec), 0, at<StateFast>(ws, x->L.sfast),
                    at<double>(ws, x->L.qpart), at<double>(ws, x->L.qres) + 4 * slot, ws->err, s);
+  // the energy codes depend on E only; rebuilt whenever the state table is
+  if (slot == 0) launch_state_codes(st, at<code_t>(ws, x->L.code), at<unsigned long long>(ws, x->L.qwords), s);
   ws->cache_valid = allow_cache ? 1 : 0;
   ws->cache_E = st->E; ws->cache_n = st->n; ws->cache_T = c.T; ws->cache_Tv = c.T_vib;
+}
+
+const QuantHdr* qhdr(pxc_workspace* ws) {
+  return reinterpret_cast<const QuantHdr*>(at<unsigned long long>(ws, X(ws)->L.qwords) + kQuantWords);
 }
 
 BoundP make_bound(const pxc_condition& c, double threshold) {
@@ -287,16 +295,17 @@ pxc_status front_plain(pxc_workspace* ws, const pxc_states* st, const pxc_transi
   unsigned long long* cnt = at<unsigned long long>(ws, L.counters);
   run_boltzmann(ws, st, c, 0, s, ws->accumulate != 0);
   cudaMemsetAsync(at<unsigned long long>(ws, L.maxbits), 0, 8, s);
-  const int64_t nblk = (tr->n + kLinesPerBlockI - 1) / kLinesPerBlockI;
+  const int64_t nunit = (tr->n + kUnitLines - 1) / kUnitLines;
   tmark(ws, 0, true, s);
   BoundP bp = make_bound(c, threshold);
-  launch_lines_compact(tr, st->n, at<StateFast>(ws, L.sfast), at<double2>(ws, L.srec), at<double>(ws, L.qres), gp,
-                       threshold, bp, 1, at<uint64_t>(ws, L.key), at<uint32_t>(ws, L.sidx1), at<double>(ws, L.Iv),
-                       at<uint32_t>(ws, L.bcount), nblk, at<unsigned long long>(ws, L.maxbits), ws->err, s);
+  launch_lines_compact(tr, st->n, at<code_t>(ws, L.code), qhdr(ws), at<StateFast>(ws, L.sfast),
+                       at<double2>(ws, L.srec), at<double>(ws, L.qres), gp, threshold, bp, 1, at<uint64_t>(ws, L.key),
+                       at<uint32_t>(ws, L.sidx1), at<double>(ws, L.Iv), at<uint32_t>(ws, L.bcount), nunit,
+                       at<unsigned long long>(ws, L.maxbits), ws->err, s);
   tmark(ws, 0, false, s);
   tmark(ws, 1, true, s);
-  if (nblk) launch_scan_counts(at<uint32_t>(ws, L.bcount), nblk, cnt + CNT_KEPT, s);
-  launch_compact_staged(at<uint64_t>(ws, L.key), at<uint32_t>(ws, L.sidx1), at<uint32_t>(ws, L.bcount), nblk,
+  if (nunit) launch_scan_counts(at<uint32_t>(ws, L.bcount), nunit, cnt + CNT_KEPT, s);
+  launch_compact_staged(at<uint64_t>(ws, L.key), at<uint32_t>(ws, L.sidx1), at<uint32_t>(ws, L.bcount), nunit,
                         at<uint64_t>(ws, L.skey0), at<uint32_t>(ws, L.sidx0), s);
   uint64_t* keys[2] = {at<uint64_t>(ws, L.skey0), at<uint64_t>(ws, L.skey1)};
   uint32_t* idxs[2] = {at<uint32_t>(ws, L.sidx0), at<uint32_t>(ws, L.sidx1)};
@@ -545,13 +554,13 @@ pxc_status pxc_cross_section(pxc_workspace* ws, const pxc_states* st, const pxc_
     // geometry only: kept set from nu and the window; intensities per temperature slot in sorted order.
     // The geometry pass reads E through the state table, so fill it (first slot) first.
     run_boltzmann(ws, st, slots[0], 0, s, false);
-    const int64_t nblk = (tr->n + kLinesPerBlockI - 1) / kLinesPerBlockI;
+    const int64_t nunit = (tr->n + kUnitLines - 1) / kUnitLines;
     BoundP bp = make_bound(c[0], 0.0);
-    launch_lines_compact(tr, st->n, at<StateFast>(ws, L.sfast), at<double2>(ws, L.srec), at<double>(ws, L.qres), gp,
-                         0.0, bp, 0, at<uint64_t>(ws, L.key), idxs[1], nullptr, at<uint32_t>(ws, L.bcount), nblk,
-                         nullptr, ws->err, s);
-    if (nblk) launch_scan_counts(at<uint32_t>(ws, L.bcount), nblk, cnt + CNT_KEPT, s);
-    launch_compact_staged(at<uint64_t>(ws, L.key), idxs[1], at<uint32_t>(ws, L.bcount), nblk, keys[0], idxs[0], s);
+    launch_lines_compact(tr, st->n, at<code_t>(ws, L.code), qhdr(ws), at<StateFast>(ws, L.sfast),
+                         at<double2>(ws, L.srec), at<double>(ws, L.qres), gp, 0.0, bp, 0, at<uint64_t>(ws, L.key),
+                         idxs[1], nullptr, at<uint32_t>(ws, L.bcount), nunit, nullptr, ws->err, s);
+    if (nunit) launch_scan_counts(at<uint32_t>(ws, L.bcount), nunit, cnt + CNT_KEPT, s);
+    launch_compact_staged(at<uint64_t>(ws, L.key), idxs[1], at<uint32_t>(ws, L.bcount), nunit, keys[0], idxs[0], s);
     launch_radix_sort(keys, idxs, cnt + CNT_KEPT, tr->n, at<uint32_t>(ws, L.rcount), s);
     launch_prepare(keys[0], idxs[0], cnt + CNT_KEPT, tr->n, gp, pa->gamma_ref, pa->n_T, nullptr, kexp,
                    at<int4>(ws, L.pos), at<float2>(ws, L.par), nullptr, tr, at<int32_t>(ws, L.su),

@@ -33,6 +33,7 @@ constexpr uint64_t kSentinelKey = ~0ull;  // sorts after every positive double
 // ---------------------------------------------------------------- launch geometry
 constexpr int kLinesPerBlockI = 2048;     // lines per CTA in the intensity pass (256 x 8)
 constexpr int kThreadsI = 256;
+constexpr int kUnitLines = 2048;         // lines per warp unit in the compacting intensity pass
 constexpr int kSortTile = 4096;           // keys per CTA in a radix pass (256 threads x 16)
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = kSortTile / kSortThreads;

@@ -364,3 +364,53 @@ def test_full_size_chunk_sampled_windows(pxc):
         big = ref > 1e-6 * peak
         assert np.all(d[big] / ref[big] <= H.SIG_REL), f"window {i0}: {np.max(d[big] / ref[big])}"
     del torch
+
+
+# ------------------------------------------------------------------ state-code prefilter edges
+
+def _edge_case(rng_seed, threshold_quantile, E_offset):
+    """States in pairs whose nu lands within +-0.05 cm^-1 of the kept window's ends (and spread
+    over it), plus random pairs; threshold at a quantile of |I| so many lines sit near it."""
+    rng = np.random.default_rng(rng_seed)
+    n_pair = 6000
+    w = H.synth.workload("doppler_1e5").scaled(n_states=2 * n_pair + 4000, n_trans=0, nu_min=1000.0, dnu=0.01,
+                                                n_grid=100_001, T=900.0, cutoff=5.0, threshold=0.0)
+    lo_edge, hi_edge = w.nu_min - w.cutoff, w.nu_min + (w.n_grid - 1) * w.dnu + w.cutoff
+    targets = np.concatenate([lo_edge + rng.uniform(-0.05, 0.05, n_pair // 3),
+                              hi_edge + rng.uniform(-0.05, 0.05, n_pair // 3),
+                              rng.uniform(lo_edge - 50.0, hi_edge + 50.0, n_pair - 2 * (n_pair // 3))])
+    El = rng.uniform(0.0, 40000.0, n_pair) + E_offset
+    E = np.empty(w.n_states)
+    E[0:2 * n_pair:2] = El
+    E[1:2 * n_pair:2] = El + targets
+    E[2 * n_pair:] = rng.uniform(0.0, 45000.0, w.n_states - 2 * n_pair) + E_offset
+    g = rng.integers(1, 60, w.n_states).astype(np.int32)
+    up = np.concatenate([np.arange(1, 2 * n_pair, 2), rng.integers(0, w.n_states, 30000)]).astype(np.int32)
+    lo = np.concatenate([np.arange(0, 2 * n_pair, 2), rng.integers(0, w.n_states, 30000)]).astype(np.int32)
+    A = 10.0 ** rng.uniform(-6, 2, up.size)
+    c = {"w": w.scaled(n_trans=up.size), "E": E, "g": g, "Ev": np.zeros(w.n_states), "up": up, "lo": lo, "A": A,
+         "gr": np.full(up.size, 0.05, np.float32), "ne": np.full(up.size, 0.5, np.float32)}
+    if threshold_quantile is not None:
+        r0 = H.oracle_run(c, threshold=0.0, with_sigma=False)
+        Ik = np.sort(np.abs(r0["I"][r0["keep"].astype(bool)]))
+        j = int(threshold_quantile * (Ik.size - 1))
+        while Ik[j + 1] <= Ik[j] * (1 + 1e-6):  # no line within rounding of the threshold
+            j += 1
+        c["w"] = c["w"].scaled(threshold=float(np.sqrt(Ik[j] * Ik[j + 1])))
+    return c
+
+
+@pytest.mark.parametrize("seed,q,off", [(1, None, 0.0), (2, 0.5, 0.0), (3, 0.9, -75.0), (4, 0.2, 1234.5)])
+def test_prefilter_keeps_exact_set_at_window_and_threshold_edges(pxc, seed, q, off):
+    c = _edge_case(seed, q, off)
+    w = c["w"]
+    ws = _ws(pxc, c)
+    st, tr, prof, grid = H.device(c)
+    sig, e = pxc.pxc_cross_section(ws, st, tr, (w.T, 0.0, w.P), grid, prof, w.threshold)
+    s = ws.stats()
+    r = H.oracle_run(c)
+    keep = r["keep"].astype(bool)
+    assert s["n_kept"] == int(keep.sum())
+    perm, _, _ = ws.binning(s["n_kept"], s["n_segments"])
+    assert np.array_equal(perm.cpu().numpy(), r["perm"])
+    H.check_sigma(H.sigma_phys(sig[0], e[0].item()), r["sigma"], f"prefilter edges {seed}")
