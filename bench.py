@@ -36,6 +36,7 @@ sys.path.insert(0, ROOT)
 METRIC = "Voigt line-grid evals/s & lines/s at 1e9 lines; batched, fwd+bwd vs plain"
 UNIT = "line-grid evals/s"
 EVAL_FP32_OPS = 6      # FP32-pipe instructions of one region-I Voigt evaluation (fast path)
+SFU_PER_SM_CLK = 16    # MUFU (rcp/ex2) results per SM per clock; every evaluation needs one
 L2_BYTES = 126 * 2 ** 20
 
 # DRAM traffic per profile-kernel launch from the committed ncu capture, valid only for
@@ -330,26 +331,35 @@ def main_pxc(args):
     sms = props.multi_processor_count
     sm_max = float(clk.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2032.0))
     alu_peak = sms * 128 * sm_max * 1e6 / 1e12            # T FP32 lane-ops/s
+    sfu_peak = sms * SFU_PER_SM_CLK * sm_max * 1e6 / 1e9   # G evaluations/s (one MUFU op each)
     prof_ms, prof_n = tm["profile"]
     int_ms, int_n = tm["intensity"]
     sort_ms, sort_n = tm["sort"]
-    per_launch_ops = EVAL_FP32_OPS * evals / nchunks
+    per_launch_evals = evals / nchunks
     prof_launch_ms = prof_ms / max(prof_n, 1)
-    ach_alu = per_launch_ops / (prof_launch_ms / 1e3) / 1e12
-    per_launch_bytes = (chunk * (4 + 4 + (4 if w.A_f32 else 8)) + chunk * (8 + 8))
+    ach_evals = per_launch_evals / (prof_launch_ms / 1e3) / 1e9
+    ach_alu = EVAL_FP32_OPS * per_launch_evals / (prof_launch_ms / 1e3) / 1e12
+    # algorithmic bytes of one intensity launch: the line arrays read once (upper, lower, A),
+    # (key, index, FP64 I) written per kept line, and the 2-byte state-code table read once
+    kept_per_launch = kept / nchunks
+    per_launch_bytes = chunk * (4 + 4 + (4 if w.A_f32 else 8)) + kept_per_launch * (8 + 4 + 8) + w.n_states * 2
     int_launch_ms = int_ms / max(int_n, 1)
     ach_hbm = per_launch_bytes / (int_launch_ms / 1e3) / 1e9
     kvh = _src_hash("paper_2609_17273_b300/csrc/kernels_profile.cu")
     klh = _src_hash("paper_2609_17273_b300/csrc/kernels_lines.cu")
     tr_prof = NCU_TRAFFIC.get(("profile", kvh))
     tr_int = NCU_TRAFFIC.get(("intensity", klh))
-    roof_profile = {"bound": "alu", "achieved": ach_alu, "peak": alu_peak, "unit": "T FP32 lane-ops/s",
-                    "frac": ach_alu / alu_peak, "traffic": tr_prof, "kernel": "k_profile<VOIGT>",
-                    "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz",
-                    "ops_per_eval": EVAL_FP32_OPS, "launch_ms": prof_launch_ms}
+    roof_profile = {"bound": "alu", "achieved": ach_evals, "peak": sfu_peak, "unit": "G evals/s",
+                    "frac": ach_evals / sfu_peak, "traffic": tr_prof, "kernel": "k_profile<VOIGT>",
+                    "peak_source": f"{sms} SMs x {SFU_PER_SM_CLK} MUFU results/clk x {sm_max:.0f} MHz "
+                                   "(one rcp per region-I evaluation)",
+                    "fp32_lane_ops": {"achieved_T": ach_alu, "peak_T": alu_peak, "frac": ach_alu / alu_peak,
+                                      "ops_per_eval": EVAL_FP32_OPS},
+                    "launch_ms": prof_launch_ms}
     roof_int = {"bound": "hbm", "achieved": ach_hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach_hbm / peaks["hbm_gbs"], "traffic": tr_int, "kernel": "k_lines",
+                "frac": ach_hbm / peaks["hbm_gbs"], "traffic": tr_int, "kernel": "k_lines_c",
                 "peak_source": f"hbm_gbs of {peak_src}", "bytes_per_line": per_launch_bytes / chunk,
+                "sector_bytes_per_line": 4 + 4 + (4 if w.A_f32 else 8) + 2 * 32,
                 "launch_ms": int_launch_ms}
     dominant = roof_profile if prof_ms >= int_ms else roof_int
 

@@ -167,31 +167,42 @@ __device__ __noinline__ void w4_full(float x, float y, cplx* w, cplx* dw) {
 
 // Real part of W4 in regions II-IV (|x| + y < 15), forward only.  Kept out of line so the
 // branch-free far-wing loop of the profile kernel stays small in registers.
-__device__ __noinline__ float w4_core_re(float x, float y) {
-  const float ax = fabsf(x), s = ax + y;
+// W4 region III (|x|+y < 5.5, y >= 0.195|x| - 0.176): a degree-5 rational in t = y - ix.
+__device__ __forceinline__ float w4_reg3_re(float x, float y) {
+  const cplx t = {y, -x};
+  cplx P = cadd(cmul(t, cadd(cmul(t, cadd(cmul(t, cadd(cmul(t, {0.5642236f, 0.f}), 3.778987f)), 11.96482f)), 20.20933f)),
+                16.4955f);
+  cplx Q = cadd(cmul(t, cadd(cmul(t, cadd(cmul(t, cadd(cmul(t, cadd(t, 6.699398f)), 21.69274f)), 39.27121f)),
+                             38.82363f)),
+                16.4955f);
+  return cdiv(P, Q).r;
+}
+
+// W4 region IV (the rest of |x|+y < 5.5): w = exp(u) - t P(u)/Q(u), u = t^2.  The hardware
+// exp2/cos approximations cost ~1e-6 absolute in e^Re(u) cos(Im u) for |Im u| <= 11 here,
+// two orders below the W4 accuracy.
+__device__ __forceinline__ float w4_reg4_re(float x, float y) {
   const cplx t = {y, -x};
   const cplx u = cmul(t, t);
-  if (s >= 5.5f) {
-    // w = t (1.410474 + 0.5641896 u) / (0.75 + u (3 + u))
-    cplx N = {1.410474f + 0.5641896f * u.r, 0.5641896f * u.i};
-    cplx D = cadd(cmul(u, cadd(u, 3.f)), 0.75f);
-    return cdiv(cmul(t, N), D).r;
-  }
-  if (y >= 0.195f * ax - 0.176f) {
-    cplx P = cadd(cmul(t, cadd(cmul(t, cadd(cmul(t, cadd(cmul(t, {0.5642236f, 0.f}), 3.778987f)), 11.96482f)), 20.20933f)),
-                  16.4955f);
-    cplx Q = cadd(cmul(t, cadd(cmul(t, cadd(cmul(t, cadd(cmul(t, cadd(t, 6.699398f)), 21.69274f)), 39.27121f)),
-                               38.82363f)),
-                  16.4955f);
-    return cdiv(P, Q).r;
-  }
   cplx P = csub_from(36183.31f, cmul(u, csub_from(3321.9905f, cmul(u, csub_from(1540.787f, cmul(u, csub_from(219.0313f,
                cmul(u, csub_from(35.76683f, cmul(u, csub_from(1.320522f, {0.56419f * u.r, 0.56419f * u.i})))))))))));
   cplx Q = csub_from(32066.6f, cmul(u, csub_from(24322.84f, cmul(u, csub_from(9022.228f, cmul(u, csub_from(2186.181f,
                cmul(u, csub_from(364.2191f, cmul(u, csub_from(61.57037f, cmul(u, csub_from(1.841439f, u)))))))))))));
-  const float eu = expf(u.r);
-  const float cs = cosf(u.i);
-  return eu * cs - cmul(t, cdiv(P, Q)).r;
+  return __expf(u.r) * __cosf(u.i) - cmul(t, cdiv(P, Q)).r;
+}
+
+__device__ __noinline__ float w4_core_re(float x, float y) {
+  const float ax = fabsf(x), s = ax + y;
+  if (s >= 5.5f) {
+    // w = t (1.410474 + 0.5641896 u) / (0.75 + u (3 + u))
+    const cplx t = {y, -x};
+    const cplx u = cmul(t, t);
+    cplx N = {1.410474f + 0.5641896f * u.r, 0.5641896f * u.i};
+    cplx D = cadd(cmul(u, cadd(u, 3.f)), 0.75f);
+    return cdiv(cmul(t, N), D).r;
+  }
+  if (y >= 0.195f * ax - 0.176f) return w4_reg3_re(x, y);
+  return w4_reg4_re(x, y);
 }
 
 // Real part of W4 in every region (used by the general path).
@@ -213,13 +224,16 @@ __device__ __forceinline__ float w4_re(float x, float y) {
 // picks one per profile kind (pxc_autotune times them on the caller's inputs).
 
 struct __align__(16) LineC {
-  float pf, step, nfs, B1;     // centre offset (grid steps, exact integer part), step, -f*step, 2y^2-1 | gamma^2
-  float A2, K, KA, y;          // region-I constants (Voigt), Lorentz/Gauss amplitude in K
+  // fast-path constants, first so that two 16-byte loads fetch them:
+  //   Voigt:   a = x at lane 0 of the owning warp, b = step, B1 = 2y^2 - 1, d = A2
+  //   others:  a = wbase - pf (exact integer), b = step, B1 = gamma^2 (Lorentz) or 0, d = nfs
+  float a, b, B1, d;
+  float K, KA, y, Kc;          // amplitudes (K: fast/region I, Kc: general path), y (Voigt) or gamma
+  float pf, step, nfs, reach;  // centre offset (grid steps, exact integer part), step, -f*step;
+                               // half-width of the non-region-I zone (grid steps)
   int lo, hi;                  // window relative to the segment (grid points, clamped)
   int masks;                   // 1 if the line is valid with non-zero intensity and a non-empty window; then its class
-  float Kc;                    // amplitude of the general path
-  float reach, cen;            // half-width of the non-region-I zone and the centre (grid steps)
-  float pad0, pad1;
+  float cen;                   // the centre (grid steps from the segment start)
 };
 
 // Smallest Doppler HWHM used (cm^-1).  Keeps the scaled FP32 arithmetic finite for lines with
@@ -229,9 +243,13 @@ constexpr float kAlphaMin = 8.4e-8f;
 // Smallest Lorentz HWHM used (cm^-1): gamma^2 stays a normal FP32 number.
 constexpr float kGammaMin = 1e-15f;
 
+// Per-line constants for the warp owning points [wbase, wbase + 32 PTS) of the segment.  All
+// FP32: the centre wavenumber that scales the Doppler width is rebuilt from the grid index and
+// fraction (relative error ~1e-7, far below the profile tolerance); reciprocals are the
+// hardware approximation (<= 1 ulp), and the region-I reach is widened by 1e-4 to stay safe.
 template <int KIND, int SEG>
 __device__ __forceinline__ void line_constants(const int4 p4, const float2 pr, const float is, const CondDev& cd,
-                                               int64_t i0, float dnu_f, double nu_min, double dnu, bool valid,
+                                               int64_t i0, int wbase, float dnu_f, float nu_min_f, bool valid,
                                                LineC& c) {
   const int ic = p4.x;
   const float f = __int_as_float(p4.y);
@@ -248,11 +266,14 @@ __device__ __forceinline__ void line_constants(const int4 p4, const float2 pr, c
     c.B1 = g * g;
     c.Kc = is * g * kInvPi;
     c.K = c.Kc;
-    c.A2 = 0.f; c.KA = 0.f; c.y = g;
+    c.KA = 0.f; c.y = g;
+    c.a = (float)wbase - c.pf;
+    c.b = c.step;
+    c.d = c.nfs;
   } else {
-    const float nu = (float)(nu_min + ((double)ic + (double)f) * dnu);
+    const float nu = fmaf((float)ic + f, dnu_f, nu_min_f);
     const float alpha = fmaxf(KIND == PXC_GAUSS_HWHM ? cd.hwhm : cd.alpha_coef * nu, kAlphaMin);
-    const float cc = kSqrtLn2 / alpha;       // 1 / (s sqrt 2)
+    const float cc = kSqrtLn2 * frcp(alpha);  // 1 / (s sqrt 2)
     if (KIND == PXC_VOIGT) {
       const float g = pr.x * exp2f(pr.y * cd.log2_tratio) * cd.P_f;
       const float y = g * cc;
@@ -261,11 +282,13 @@ __device__ __forceinline__ void line_constants(const int4 p4, const float2 pr, c
       c.nfs = -f * c.step;
       const float A = 0.5f + y * y;
       c.B1 = 2.f * y * y - 1.f;
-      c.A2 = A * A;
+      c.d = A * A;
       c.Kc = is * cc * kInvSqrtPi;
       c.K = c.Kc * y * kInvSqrtPi;
       c.KA = c.K * A;
-      reach = fmaxf(15.f - y, 0.f) / c.step;
+      reach = fmaxf(15.f - y, 0.f) * frcp(c.step) * 1.0001f;
+      c.a = fmaf((float)wbase - c.pf, c.step, c.nfs);
+      c.b = c.step;
     } else {
       // exp(-X^2) = 2^(-(X sqrt(log2 e))^2); x is scaled by sqrt(log2 e)
       const float sl2e = 1.2011224087864498f;
@@ -273,9 +296,13 @@ __device__ __forceinline__ void line_constants(const int4 p4, const float2 pr, c
       c.nfs = -f * c.step;
       c.Kc = is * cc * kInvSqrtPi;
       c.K = c.Kc;
-      c.y = 0.f; c.B1 = 0.f; c.A2 = 0.f; c.KA = 0.f;
-      // provably-zero trim: 2^(-t) for t > 159 is below the FP32 range of every product here
-      const float r = 12.7f / c.step;        // |X'| <= 12.7 <=> X^2 <= 111.8
+      c.y = 0.f; c.B1 = 0.f; c.KA = 0.f;
+      c.a = (float)wbase - c.pf;
+      c.b = c.step;
+      c.d = c.nfs;
+      // provably-zero trim: ex2.approx.ftz flushes 2^(-t) to 0 for t > 126, and |X'| >= 12.7
+      // (rounded reciprocal included) gives t >= 161
+      const float r = 12.7f * frcp(c.step);
       const float elo = ceilf(cen - r), ehi = floorf(cen + r);
       if (elo > (float)c.lo) c.lo = (int)fminf(elo, (float)SEG);
       if (ehi < (float)c.hi) c.hi = (int)fmaxf(ehi, -1.f);
@@ -309,31 +336,28 @@ __device__ __forceinline__ float eval_general(float x, const LineC& c) {
   return c.K * fex2(-(x * x));
 }
 
-// Branch-free evaluation of one line at the lane's PTS points (fast class).
+// Branch-free evaluation of one line at the lane's PTS points (fast class); lk[k] = lane + 32 k.
 template <int KIND, int PTS>
-__device__ __forceinline__ void eval_fast(const LineC& c, float lane_f, float* acc) {
+__device__ __forceinline__ void eval_fast(const LineC& c, const float* lk, float* acc) {
+  const float4 f0 = *reinterpret_cast<const float4*>(&c.a);  // a, b, B1, d
+  const float K = c.K;
   if (KIND == PXC_VOIGT) {
     // far wing, W4 region I: Re w = y (A + x^2) / (sqrt(pi) ((A - x^2)^2 + 4 x^2 y^2)), A = 1/2 + y^2;
-    // no point of this warp is near the centre, so x = x0 + 32 k step keeps full relative accuracy
-    const float4 f0 = *reinterpret_cast<const float4*>(&c.pf);   // pf, step, nfs, B1
-    const float4 f1 = *reinterpret_cast<const float4*>(&c.A2);   // A2, K, KA, y
-    const float x0 = fmaf(lane_f - f0.x, f0.y, f0.z);
-    const float s32 = 32.f * f0.y;
+    // no point of this warp is near the centre, so x = x(lane 0) + m step keeps full relative accuracy
+    const float KA = c.KA;
 #pragma unroll
     for (int k = 0; k < PTS; ++k) {
-      const float x = fmaf((float)k, s32, x0);
+      const float x = fmaf(lk[k], f0.y, f0.x);
       const float x2 = x * x;
-      const float den = fmaf(x2, x2 + f0.w, f1.x);
-      acc[k] = fmaf(fmaf(x2, f1.y, f1.z), frcp(den), acc[k]);
+      const float den = fmaf(x2, x2 + f0.z, f0.w);
+      acc[k] = fmaf(fmaf(x2, K, KA), frcp(den), acc[k]);
     }
   } else {
     // the line centre may lie among these points: x from the exact integer offset
-    const float4 f0 = *reinterpret_cast<const float4*>(&c.pf);
-    const float K = c.K;
 #pragma unroll
     for (int k = 0; k < PTS; ++k) {
-      const float x = fmaf(lane_f + (float)(32 * k) - f0.x, f0.y, f0.z);
-      if (KIND == PXC_LORENTZ) acc[k] = fmaf(K, frcp(fmaf(x, x, f0.w)), acc[k]);
+      const float x = fmaf(lk[k] + f0.x, f0.y, f0.w);
+      if (KIND == PXC_LORENTZ) acc[k] = fmaf(K, frcp(fmaf(x, x, f0.z)), acc[k]);
       else acc[k] = fmaf(K, fex2(-(x * x)), acc[k]);
     }
   }
@@ -341,22 +365,20 @@ __device__ __forceinline__ void eval_fast(const LineC& c, float lane_f, float* a
 
 // Two lines at once (more independent work per point, half the loop overhead).
 template <int KIND, int PTS>
-__device__ __forceinline__ void eval_fast2(const LineC& c, const LineC& d, float lane_f, float* acc) {
+__device__ __forceinline__ void eval_fast2(const LineC& c, const LineC& e, const float* lk, float* acc) {
   if (KIND == PXC_VOIGT) {
-    const float4 a0 = *reinterpret_cast<const float4*>(&c.pf), a1 = *reinterpret_cast<const float4*>(&c.A2);
-    const float4 b0 = *reinterpret_cast<const float4*>(&d.pf), b1 = *reinterpret_cast<const float4*>(&d.A2);
-    const float xa = fmaf(lane_f - a0.x, a0.y, a0.z), sa = 32.f * a0.y;
-    const float xb = fmaf(lane_f - b0.x, b0.y, b0.z), sb = 32.f * b0.y;
+    const float4 a0 = *reinterpret_cast<const float4*>(&c.a), a1 = *reinterpret_cast<const float4*>(&c.K);
+    const float4 b0 = *reinterpret_cast<const float4*>(&e.a), b1 = *reinterpret_cast<const float4*>(&e.K);
 #pragma unroll
     for (int k = 0; k < PTS; ++k) {
-      const float x = fmaf((float)k, sa, xa), y = fmaf((float)k, sb, xb);
+      const float x = fmaf(lk[k], a0.y, a0.x), y = fmaf(lk[k], b0.y, b0.x);
       const float x2 = x * x, y2 = y * y;
-      const float ra = frcp(fmaf(x2, x2 + a0.w, a1.x)), rb = frcp(fmaf(y2, y2 + b0.w, b1.x));
-      acc[k] = fmaf(fmaf(x2, a1.y, a1.z), ra, fmaf(fmaf(y2, b1.y, b1.z), rb, acc[k]));
+      const float ra = frcp(fmaf(x2, x2 + a0.z, a0.w)), rb = frcp(fmaf(y2, y2 + b0.z, b0.w));
+      acc[k] = fmaf(fmaf(x2, a1.x, a1.y), ra, fmaf(fmaf(y2, b1.x, b1.y), rb, acc[k]));
     }
   } else {
-    eval_fast<KIND, PTS>(c, lane_f, acc);
-    eval_fast<KIND, PTS>(d, lane_f, acc);
+    eval_fast<KIND, PTS>(c, lk, acc);
+    eval_fast<KIND, PTS>(e, lk, acc);
   }
 }
 
@@ -372,7 +394,7 @@ __device__ __forceinline__ void eval_fastmask(const LineC& c, int wbase, int lan
     for (int k = 0; k < PTS; ++k) {
       const float x = fmaf((float)k, s32, x0);
       const float x2 = x * x;
-      const float den = fmaf(x2, x2 + c.B1, c.A2);
+      const float den = fmaf(x2, x2 + c.B1, c.d);
       const float v = fmaf(x2, c.K, c.KA) * frcp(den);
       acc[k] += (unsigned)(rel0 + 32 * k) <= span ? v : 0.f;
     }
@@ -386,14 +408,8 @@ __device__ __forceinline__ void eval_fastmask(const LineC& c, int wbase, int lan
   }
 }
 
-// Warps near the line core (Voigt): blocks of 32 points far from the centre keep the
-// region-I formula; elsewhere each point takes its W4 region.  Region II
-// (5.5 <= |x|+y < 15) is evaluated as the real rational Re w = y N(X) / D(X) in X = x^2
-// (N cubic, D monic quartic, coefficients from Y = y^2 once per line and warp; Humlicek's
-// constants satisfy a = 2.5 b, which gives the factored forms below); only |x|+y < 5.5
-// needs the complex regions III/IV.
 template <int KIND, int PTS>
-__device__ __forceinline__ void eval_slow(const LineC& c, int wbase, int lane, float* acc) {
+__device__ __forceinline__ void eval_slow(const LineC& c, int wbase, int lane, const float* lk, float* acc) {
   const unsigned span = (unsigned)(c.hi - c.lo);
   const float bq = 0.5641896f;
   const float Y = c.y * c.y;
@@ -407,13 +423,22 @@ __device__ __forceinline__ void eval_slow(const LineC& c, int wbase, int lane, f
     const int b0 = wbase + 32 * k;
     if (b0 > c.hi || b0 + 31 < c.lo) continue;
     const int li = b0 + lane;
-    const float x = fmaf((float)li - c.pf, c.step, c.nfs);
     const bool in = (unsigned)(li - c.lo) <= span;
     const float dmin = fmaxf(0.f, fmaxf(c.cen - (float)(b0 + 31), (float)b0 - c.cen));
+    if (PTS >= 8 && dmin > c.reach) {
+      // the whole block is in region I (uniform branch): the fast-path formula (measured to pay
+      // off for wide warps only; narrow ones rarely have such blocks among their slow lines)
+      const float x = fmaf(lk[k], c.b, c.a);
+      const float x2 = x * x;
+      const float v = fmaf(x2, c.K, c.KA) * frcp(fmaf(x2, x2 + c.B1, c.d));
+      acc[k] += in ? v : 0.f;
+      continue;
+    }
+    const float x = fmaf((float)li - c.pf, c.step, c.nfs);
     float v;
     const float x2 = x * x;
-    if (dmin > c.reach || fabsf(x) + c.y >= 15.f) {
-      v = fmaf(x2, c.K, c.KA) * frcp(fmaf(x2, x2 + c.B1, c.A2));
+    if (fabsf(x) + c.y >= 15.f) {
+      v = fmaf(x2, c.K, c.KA) * frcp(fmaf(x2, x2 + c.B1, c.d));
     } else if (fabsf(x) + c.y >= 5.5f) {
       const float N = fmaf(fmaf(fmaf(n3, x2, n2), x2, n1), x2, n0);
       const float D = fmaf(fmaf(fmaf(x2 + d3, x2, d2), x2, d1), x2, d0);
@@ -454,7 +479,9 @@ __global__ void __launch_bounds__(THREADS, MINB) k_profile(const ProfP p) {
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int wbase = warp * WPTS;
-  const float lane_f = (float)(wbase + lane);
+  float lk[PTS];  // lane + 32 k
+#pragma unroll
+  for (int k = 0; k < PTS; ++k) lk[k] = (float)(lane + 32 * k);
   const unsigned lt = (1u << lane) - 1u;
   LineC* my = wl + warp * SL;
   if (tid == 0) {
@@ -465,7 +492,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_profile(const ProfP p) {
   __syncthreads();
   unsigned phase = 0;  // bit b: parity this warp waits for next on buffer b
   const unsigned long long n_items = *p.n_items;
-  const float dnu_f = (float)p.dnu;
+  const float dnu_f = (float)p.dnu, nu_min_f = (float)p.nu_min;
 
   for (int iter = 0;; ++iter) {
     if (tid == 0) {
@@ -517,7 +544,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_profile(const ProfP p) {
         const float2 pr = reinterpret_cast<const float2*>(src + SL * 16)[j];
         const float is = reinterpret_cast<const float*>(src + SL * 24)[j];
         LineC c;
-        line_constants<KIND, SEG>(p4, pr, is, cd, i0, dnu_f, p.nu_min, p.dnu, J >= item.begin && J < item.end, c);
+        line_constants<KIND, SEG>(p4, pr, is, cd, i0, wbase, dnu_f, nu_min_f, J >= item.begin && J < item.end, c);
         const int cls = line_class<KIND, WPTS>(c, wbase);
         c.masks = cls;
         const unsigned bf = __ballot_sync(0xffffffffu, cls == 1);
@@ -544,12 +571,12 @@ __global__ void __launch_bounds__(THREADS, MINB) k_profile(const ProfP p) {
 #pragma unroll
       for (int k = 0; k < PTS; ++k) acc[k] = 0.f;
       int i = 0;
-      for (; i + 1 < nf; i += 2) eval_fast2<KIND, PTS>(my[i], my[i + 1], lane_f, acc);
-      if (i < nf) eval_fast<KIND, PTS>(my[i], lane_f, acc);
+      for (; i + 1 < nf; i += 2) eval_fast2<KIND, PTS>(my[i], my[i + 1], lk, acc);
+      if (i < nf) eval_fast<KIND, PTS>(my[i], lk, acc);
       for (int q = SL - 1; q >= SL - no; --q) {
         const LineC& c = my[q];
         if (c.masks == 2) eval_fastmask<KIND, PTS>(c, wbase, lane, acc);
-        else eval_slow<KIND, PTS>(c, wbase, lane, acc);
+        else eval_slow<KIND, PTS>(c, wbase, lane, lk, acc);
       }
 #pragma unroll
       for (int k = 0; k < PTS; ++k) sum[k] += acc[k];
