@@ -41,7 +41,7 @@ L2_BYTES = 126 * 2 ** 20
 
 # DRAM traffic per profile-kernel launch from the committed ncu capture, valid only for
 # the kernel source it was taken on (sha256 prefix of kernels_profile.cu).
-# Taken from profiles/k_*_voigt_2e7_lines.md (a 2e7-line capture scaled x5 to one 1e8-line launch).
+# Both come from an ncu capture of the 2e7-line case, scaled x5 to one 1e8-line launch.
 NCU_TRAFFIC = {("profile", "aab450f67e1936e6"): 90458960, ("intensity", "69838b0667db9866"): 9578438240}
 
 
