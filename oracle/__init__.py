@@ -50,6 +50,10 @@ def _load():
         L.orc_partition.argtypes = [P, P, P, i64, dbl, dbl, P]
         L.orc_line_intensities.argtypes = [P, P, P, i64, P, P, P, cint, i64, dbl, dbl, dbl,
                                            dbl, dbl, i64, dbl, dbl, P, P, P, P, P]
+        L.orc_partition_density.argtypes = [P, P, P, P, i64, dbl, P]
+        L.orc_intensities.argtypes = [cint, P, P, P, P, i64, P, P, P, cint, i64, dbl, dbl, dbl,
+                                      dbl, dbl, i64, dbl, dbl, P, P, P, P, P]
+        L.orc_cooling_function.argtypes = [P, P, P, P, i64, P, P, P, cint, i64, dbl, dbl, dbl, P]
         L.orc_list_exponent.argtypes = [P, P, i64]
         L.orc_list_exponent.restype = ctypes.c_int32
         L.orc_scale_intensities.argtypes = [P, P, i64, ctypes.c_int32, P]
@@ -126,6 +130,43 @@ def line_intensities(E, g, E_vib, upper, lower, A, T, T_vib, Q, nu_min, dnu, n_g
                                       T, T_vib, Q, nu_min, dnu, n_grid, cut, threshold,
                                       _p(nu), _p(I), _p(keep), _p(ilo), _p(ihi)))
     return nu, I, keep, ilo, ihi
+
+
+def partition_density(E, g, E_vib, n_vib, T_rot):
+    """(Q, dQ/dT_rot) with vibronic densities: Eq. (Q nlte Nvib)."""
+    E = _c(E, np.float64); g = _c(g, np.int32); Ev = _c(E_vib, np.float64); nv = _c(n_vib, np.float64)
+    out = np.zeros(2)
+    _chk(_load().orc_partition_density(_p(E), _p(g), _p(Ev), _p(nv), E.size, T_rot, _p(out)))
+    return out
+
+
+def intensities(E, g, E_vib, upper, lower, A, T, T_vib, Q, nu_min, dnu, n_grid, cut, threshold=0.0,
+                emission=False, n_vib=None):
+    """Per-transition nu, value (absorption cm/molecule or emission erg/s/sr/molecule), keep, ilo, ihi
+    for the LTE, two-temperature (T_vib > 0) or vibronic-density (n_vib given) populations."""
+    E = _c(E, np.float64); g = _c(g, np.int32); Ev = _c(E_vib, np.float64); nv = _c(n_vib, np.float64)
+    up = _c(upper, np.int32); lo = _c(lower, np.int32)
+    A_f32 = A.dtype == np.float32
+    A = _c(A, np.float32 if A_f32 else np.float64)
+    n = up.size
+    nu = np.empty(n); I = np.empty(n); keep = np.empty(n, np.uint8)
+    ilo = np.empty(n, np.int64); ihi = np.empty(n, np.int64)
+    _chk(_load().orc_intensities(int(bool(emission)), _p(E), _p(g), _p(Ev), _p(nv), E.size, _p(up), _p(lo), _p(A),
+                                 int(A_f32), n, T, T_vib, Q, nu_min, dnu, n_grid, cut, threshold,
+                                 _p(nu), _p(I), _p(keep), _p(ilo), _p(ihi)))
+    return nu, I, keep, ilo, ihi
+
+
+def cooling_function(E, g, E_vib, upper, lower, A, T, T_vib, Q, n_vib=None) -> float:
+    """W(T) in erg/s/sr/molecule: Eq. (cf), and its non-LTE forms (sum of emission intensities)."""
+    E = _c(E, np.float64); g = _c(g, np.int32); Ev = _c(E_vib, np.float64); nv = _c(n_vib, np.float64)
+    up = _c(upper, np.int32); lo = _c(lower, np.int32)
+    A_f32 = A.dtype == np.float32
+    A = _c(A, np.float32 if A_f32 else np.float64)
+    W = np.zeros(1)
+    _chk(_load().orc_cooling_function(_p(E), _p(g), _p(Ev), _p(nv), E.size, _p(up), _p(lo), _p(A), int(A_f32),
+                                      up.size, T, T_vib, Q, _p(W)))
+    return float(W[0])
 
 
 def list_exponent(I, keep) -> int:
@@ -211,11 +252,20 @@ def cross_section_grad(kind, E, E_vib, upper, lower, A, nu, I, alpha, gamma, n_T
 
 
 def run(E, g, E_vib, upper, lower, A, gamma_ref, n_T, *, kind, T, T_vib=0.0, P=1.0, mass_da=18.0,
-        hwhm=0.0, nu_min, dnu, n_grid, cut, threshold=0.0, T_ref=296.0, with_sigma=True):
-    """Whole forward path: Q, per-line quantities, exponent, sort order, sigma."""
-    Qd = partition(E, g, E_vib if T_vib > 0 else None, T, T_vib)
-    nu, I, keep, ilo, ihi = line_intensities(E, g, E_vib, upper, lower, A, T, T_vib, Qd[0],
-                                             nu_min, dnu, n_grid, cut, threshold)
+        hwhm=0.0, nu_min, dnu, n_grid, cut, threshold=0.0, T_ref=296.0, with_sigma=True,
+        emission=False, n_vib=None):
+    """Whole forward path: Q, per-line quantities, exponent, sort order, sigma (absorption or
+    emission; LTE, two-temperature or vibronic-density populations)."""
+    if n_vib is not None:
+        Qd = np.append(partition_density(E, g, E_vib, n_vib, T), 0.0)
+    else:
+        Qd = partition(E, g, E_vib if T_vib > 0 else None, T, T_vib)
+    if emission or n_vib is not None:
+        nu, I, keep, ilo, ihi = intensities(E, g, E_vib, upper, lower, A, T, T_vib, Qd[0], nu_min, dnu, n_grid,
+                                            cut, threshold, emission=emission, n_vib=n_vib)
+    else:
+        nu, I, keep, ilo, ihi = line_intensities(E, g, E_vib, upper, lower, A, T, T_vib, Qd[0],
+                                                 nu_min, dnu, n_grid, cut, threshold)
     k = list_exponent(I, keep)
     I_s = scale_intensities(I, keep, k)
     perm = sorted_order(nu, keep)

@@ -15,6 +15,10 @@
  *   sigma(nu_i)          Eq. (xsec):        sum_l I_l f_l(nu_i - nu_l), |nu_i - nu_l| <= cut
  *   profiles             Table (profile): Doppler/Gaussian, Lorentzian, Voigt
  *   adjoint              analytic derivatives of the above (no counterpart in the paper)
+ *   Q(T_rot), densities  Eq. (Q nlte Nvib): sum g n_vib exp(-c2 E_rot / T_rot)
+ *   I (vibronic density) Eq. (nlte ab pop density)
+ *   epsilon (emission)   Eqs. (ems intensity lte), (nlte em 2T), (nlte em pop density)
+ *   W(T)                 Eq. (cf), cooling function  [reading R17 below for non-LTE]
  *
  * Readings where the text is silent or garbled (each also listed in the design doc):
  *   R7  nu = E' - E''; lines with nu <= 0 are dropped (nu = 0 would divide by zero).
@@ -27,6 +31,13 @@
  *   R11 line order: ascending nu bit pattern, ties by transition index.
  *   R12 per-list exponent: k = frexp exponent of max kept I; I_s = (float) ldexp(I, -k).
  *   R15 states with NaN energy are absent: skipped in Q, lines touching them dropped.
+ *   R17 the cooling function is the sum of the emission intensities of all lines
+ *       with nu > 0 (no grid window, no threshold); Eq. (cf) is its LTE case, and the
+ *       non-LTE populations of Eqs. (nlte em 2T) / (nlte em pop density) give the
+ *       non-LTE cases.
+ *   R18 vibronic densities: E_rot = E - E_vib within each manifold, T (the condition's
+ *       temperature) is T_rot, and the densities are used as given (every formula is
+ *       invariant under a common scale, so normalising them changes nothing).
  *   Doppler HWHM alpha = (nu/c) sqrt(2 N_A k_B T ln2 / M) (standard form; the
  *   formula itself is deferred by the paper to its predecessor).
  *   Lorentz HWHM gamma = gamma_ref (T_ref/T)^n P, with P used directly in the
@@ -266,6 +277,135 @@ int orc_line_intensities(const double* E, const int32_t* g, const double* E_vib,
     ihi[t] = hi;
   }
   return status;
+}
+
+/* ---------------------------------------------------------------------------
+ * Population model of a state (the factor multiplying g in Q and in the intensities):
+ *   LTE      exp(-c2 E / T)                                   Eq. (pf)
+ *   2T       exp(-c2 E_vib / T_vib) exp(-c2 E_rot / T_rot)    Eq. (Q nlte 2T)
+ *   density  n_vib exp(-c2 E_rot / T_rot)                     Eq. (Q nlte Nvib), R18
+ * Selected by n_vib != NULL (density, needs E_vib), else T_vib > 0 (2T), else LTE.
+ * Returns ORC_ERR_OVERFLOW when an exponent exceeds the double range.
+ * ------------------------------------------------------------------------ */
+static int population(const double* E, const double* E_vib, const double* n_vib, int64_t s, double T,
+                      double T_vib, double* out) {
+  const double c2 = orc_c2();
+  if (n_vib) {
+    double x = -c2 * (E[s] - E_vib[s]) / T;
+    if (x > ORC_EXP_MAX) return ORC_ERR_OVERFLOW;
+    *out = n_vib[s] * exp(x);
+  } else if (T_vib > 0.0) {
+    double xv = -c2 * E_vib[s] / T_vib, xr = -c2 * (E[s] - E_vib[s]) / T;
+    if (xv > ORC_EXP_MAX || xr > ORC_EXP_MAX || xv + xr > ORC_EXP_MAX) return ORC_ERR_OVERFLOW;
+    *out = exp(xv) * exp(xr);
+  } else {
+    double x = -c2 * E[s] / T;
+    if (x > ORC_EXP_MAX) return ORC_ERR_OVERFLOW;
+    *out = exp(x);
+  }
+  return ORC_OK;
+}
+
+/* Partition function with vibronic densities, Eq. (Q nlte Nvib): Q = sum g n_vib
+ * exp(-c2 E_rot / T_rot); out[0] = Q, out[1] = dQ/dT_rot. */
+int orc_partition_density(const double* E, const int32_t* g, const double* E_vib, const double* n_vib,
+                          int64_t n, double T_rot, double* out) {
+  if (!(T_rot > 0.0) || !E_vib || !n_vib) return ORC_ERR_ARG;
+  const double c2 = orc_c2();
+  double Q = 0.0, dQ = 0.0;
+  for (int64_t s = 0; s < n; ++s) {
+    if (isnan(E[s])) continue;
+    if (!isfinite(E[s]) || !isfinite(E_vib[s]) || !isfinite(n_vib[s])) return ORC_ERR_NONFINITE;
+    double p;
+    int st = population(E, E_vib, n_vib, s, T_rot, 0.0, &p);
+    if (st) return st;
+    double term = (double)g[s] * p;
+    Q += term;
+    dQ += term * c2 * (E[s] - E_vib[s]) / (T_rot * T_rot);
+  }
+  out[0] = Q;
+  out[1] = dQ;
+  return ORC_OK;
+}
+
+/* Absorption (emission == 0) or emission (emission == 1) intensities of every line under
+ * the population model above, with the same selection as orc_line_intensities (nu > 0,
+ * window on the grid, |value| >= threshold):
+ *   absorption, LTE      Eq. (abs intensity lte)
+ *   absorption, 2T       Eqs. (nlte v), (nlte ab 2T)      [R9]
+ *   absorption, density  Eq. (nlte ab pop density): g' A n''_vib exp(-c2 E''_rot/T_rot)
+ *                        (1 - exp(-c2 nu / T_rot)) / (8 pi c nu^2 Q)
+ *   emission, LTE        Eq. (ems intensity lte):   g' h c A nu exp(-c2 E'/T) / (4 pi Q)
+ *   emission, 2T         Eq. (nlte em 2T)
+ *   emission, density    Eq. (nlte em pop density)
+ * in cm/molecule (absorption) or erg/s/sr/molecule (emission).  Q is the model's own
+ * partition function. */
+int orc_intensities(int emission, const double* E, const int32_t* g, const double* E_vib, const double* n_vib,
+                    int64_t n_states, const int32_t* upper, const int32_t* lower, const void* A, int A_f32, int64_t n,
+                    double T, double T_vib, double Q, double nu_min, double dnu, int64_t n_grid, double cut,
+                    double threshold, double* nu_out, double* I_out, uint8_t* keep, int64_t* ilo, int64_t* ihi) {
+  if (!(T > 0.0) || !(Q > 0.0) || !(dnu > 0.0) || cut < 0.0 || n_grid < 1) return ORC_ERR_ARG;
+  if ((n_vib || T_vib > 0.0) && !E_vib) return ORC_ERR_ARG;
+  if (n_vib && T_vib > 0.0) return ORC_ERR_ARG;
+  const double c2 = orc_c2();
+  for (int64_t t = 0; t < n; ++t) {
+    int64_t u = upper[t], l = lower[t];
+    nu_out[t] = NAN; I_out[t] = 0.0; keep[t] = 0; ilo[t] = 0; ihi[t] = -1;
+    if (u < 0 || u >= n_states || l < 0 || l >= n_states) return ORC_ERR_ID;
+    double a = A_f32 ? (double)((const float*)A)[t] : ((const double*)A)[t];
+    if (!isfinite(a)) return ORC_ERR_NONFINITE;
+    double nu = E[u] - E[l];
+    nu_out[t] = nu;
+    if (!(nu > 0.0)) continue;                                  /* R7, R15 */
+    int64_t lo, hi;
+    if (!window(nu, nu_min, dnu, n_grid, cut, &lo, &hi)) continue;
+    double val, p;
+    int st;
+    if (emission) {
+      if ((st = population(E, E_vib, n_vib, u, T, T_vib, &p))) return st;
+      val = (double)g[u] * ORC_H * ORC_C * a * nu * p / (4.0 * ORC_PI * Q);
+    } else if (n_vib) {
+      if ((st = population(E, E_vib, n_vib, l, T, T_vib, &p))) return st;
+      val = (double)g[u] * a * p * (1.0 - exp(-c2 * nu / T)) / (8.0 * ORC_PI * ORC_C * nu * nu * Q);
+    } else {
+      double ev_l = 0.0, ev_u = 0.0;
+      if (T_vib > 0.0) { ev_l = E_vib[l]; ev_u = E_vib[u]; }
+      if ((st = population(E, E_vib, NULL, l, T, T_vib, &p))) return st;
+      double stim = T_vib > 0.0 ? 1.0 - exp(-c2 * ((ev_u - ev_l) / T_vib + ((E[u] - ev_u) - (E[l] - ev_l)) / T))
+                                : 1.0 - exp(-c2 * nu / T);
+      val = (double)g[u] * a * p * stim / (8.0 * ORC_PI * ORC_C * nu * nu * Q);
+    }
+    if (!(fabs(val) >= threshold)) continue;                    /* R10 */
+    I_out[t] = val;
+    keep[t] = 1;
+    ilo[t] = lo;
+    ihi[t] = hi;
+  }
+  return ORC_OK;
+}
+
+/* Cooling function, Eq. (cf) and reading R17: W = sum over lines with nu > 0 of
+ * g' h c A nu p(upper) / (4 pi Q), in erg/s/molecule/sr. */
+int orc_cooling_function(const double* E, const int32_t* g, const double* E_vib, const double* n_vib,
+                         int64_t n_states, const int32_t* upper, const int32_t* lower, const void* A, int A_f32,
+                         int64_t n, double T, double T_vib, double Q, double* W_out) {
+  if (!(T > 0.0) || !(Q > 0.0)) return ORC_ERR_ARG;
+  if ((n_vib || T_vib > 0.0) && !E_vib) return ORC_ERR_ARG;
+  double W = 0.0;
+  for (int64_t t = 0; t < n; ++t) {
+    int64_t u = upper[t], l = lower[t];
+    if (u < 0 || u >= n_states || l < 0 || l >= n_states) return ORC_ERR_ID;
+    double a = A_f32 ? (double)((const float*)A)[t] : ((const double*)A)[t];
+    if (!isfinite(a)) return ORC_ERR_NONFINITE;
+    double nu = E[u] - E[l];
+    if (!(nu > 0.0)) continue;
+    double p;
+    int st = population(E, E_vib, n_vib, u, T, T_vib, &p);
+    if (st) return st;
+    W += (double)g[u] * ORC_H * ORC_C * a * nu * p / (4.0 * ORC_PI * Q);
+  }
+  *W_out = W;
+  return ORC_OK;
 }
 
 /* R12: k = exponent of the largest kept |intensity| (max = m 2^k, 0.5 <= m < 1). */
