@@ -63,6 +63,11 @@ typedef struct {
   const int32_t* g;      /* [n] total degeneracy */
   const double* E_vib;   /* [n] cm^-1, or NULL */
   int64_t n;
+  const double* n_vib;   /* [n] custom vibronic densities (Sec. 3.1.3, Eq. Nvib), or NULL: with
+                            E_vib and a condition with T_vib <= 0, the populations are
+                            g n_vib exp(-c2 (E - E_vib) / T_rot) (Eq. F nlte Nvib), T = T_rot,
+                            Q by Eq. (Q nlte Nvib) and absorption by Eq. (nlte ab pop density).
+                            A condition with T_vib > 0 and n_vib set is PXC_ERR_ARG. */
 } pxc_states;
 
 /* Transitions (Sec. 2.3, .trans file): upper id, lower id, Einstein A.
@@ -150,6 +155,15 @@ int64_t pxc_kernel_launches(void);
  * the states must not change between chunks. */
 #define PXC_EXP_EMPTY (-2147483647 - 1)
 pxc_status pxc_set_accumulate(pxc_workspace* ws, int on);
+
+/* Emission mode (Sec. 3.2, emission intensities).  When on, pxc_line_intensities,
+ * pxc_cross_section and pxc_cross_section_streamed use emission intensities
+ * epsilon = g' h c A nu p' / (4 pi Q) in erg/s/sr/molecule, p' the upper-state
+ * population of the condition's model: Eq. (ems intensity lte), Eq. (nlte em 2T) or
+ * Eq. (nlte em pop density).  sigma is then the emission cross section sum epsilon f
+ * (erg/s/sr/molecule per cm^-1), with the same cut-off, threshold (on epsilon), sort and
+ * exponent handling.  pxc_cross_section_backward is absorption-only (PXC_ERR_ARG here). */
+pxc_status pxc_set_emission(pxc_workspace* ws, int on);
 
 /* Partition functions, Eq. (pf) (LTE) or Eq. (Q nlte 2T) (T_vib > 0), summed in
  * FP64 over all states for each of the n_c conditions.
@@ -282,6 +296,19 @@ pxc_status pxc_cross_section_streamed(pxc_workspace* ws, const pxc_states* state
                                       const pxc_grid* grid, const pxc_profile_args* prof, double threshold,
                                       void* dev_chunk_buf0, void* dev_chunk_buf1, size_t dev_chunk_bytes,
                                       float* sigma_out, int32_t* sigma_exp_out, cudaStream_t stream);
+
+/* Cooling functions, Eq. (cf): W = sum over transitions with nu = E' - E'' > 0 of
+ * g' h c A nu p' / (4 pi Q), in erg/s/sr/molecule, for each of n_c conditions (p' and Q
+ * of the condition's population model: LTE, two-temperature or vibronic densities;
+ * no grid window and no threshold).  W_out [n_c] device; Q_out [n_c] device or NULL.
+ * Computed as W = (h c / 4 pi Q) sum_s g_s p_s S_s with S_s = sum over lines leaving
+ * state s of A nu: one pass over the lines (FP64 atomic adds, so the last bits depend
+ * on their order) and one pass over the states per condition.  Needs max_conditions
+ * >= n_c.  Errors as pxc_partition_function, plus PXC_ERR_ID_RANGE and
+ * PXC_ERR_NONFINITE (latched) for bad ids or A. */
+pxc_status pxc_cooling_function(pxc_workspace* ws, const pxc_states* states, const pxc_transitions* trans,
+                                const pxc_condition* c, int32_t n_c, double* W_out, double* Q_out,
+                                cudaStream_t stream);
 
 /* Partition functions for callers that cannot allocate device memory.
  * No counterpart in the paper: this is a deployment variant of

@@ -29,7 +29,7 @@ c_i32, c_i64, c_dbl, c_ptr = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ct
 
 
 class pxc_states(ctypes.Structure):
-    _fields_ = [("E", c_ptr), ("g", c_ptr), ("E_vib", c_ptr), ("n", c_i64)]
+    _fields_ = [("E", c_ptr), ("g", c_ptr), ("E_vib", c_ptr), ("n", c_i64), ("n_vib", c_ptr)]
 
 
 class pxc_transitions(ctypes.Structure):
@@ -74,6 +74,7 @@ ABI_FUNCTIONS = [
     "pxc_cross_section_backward", "pxc_get_stats", "pxc_get_binning", "pxc_stream_buffer_bytes",
     "pxc_cross_section_streamed", "pxc_kernel_launches", "pxc_set_timing", "pxc_get_timing",
     "pxc_partition_function_noalloc", "pxc_set_tile", "pxc_get_tile", "pxc_autotune",
+    "pxc_set_emission", "pxc_cooling_function",
 ]
 
 # Profile-kernel tile configurations (segment width in grid points), as compiled into the library.
@@ -112,6 +113,9 @@ def load(path: str | None = None):
                                                  c_ptr]
     L.pxc_set_timing.argtypes = [c_ptr, ctypes.c_int]
     L.pxc_get_timing.argtypes = [c_ptr, c_ptr, c_ptr, c_ptr]
+    L.pxc_set_emission.argtypes = [c_ptr, ctypes.c_int]
+    L.pxc_cooling_function.argtypes = [c_ptr, P(pxc_states), P(pxc_transitions), P(pxc_condition), c_i32,
+                                       c_ptr, c_ptr, c_ptr]
     L.pxc_set_tile.argtypes = [c_ptr, c_i32, c_i32, c_i32]
     L.pxc_get_tile.argtypes = [c_ptr, c_i32, c_i32, P(c_i32)]
     L.pxc_autotune.argtypes = [c_ptr, P(pxc_states), P(pxc_transitions), P(pxc_condition), c_i32, P(pxc_grid),
@@ -158,14 +162,17 @@ def _dev(t, dtype, name):
 
 @dataclass
 class States:
-    """Device arrays of a .states table: E (float64), g (int32), E_vib (float64 or None)."""
+    """Device arrays of a .states table: E (float64), g (int32), E_vib (float64 or None), and
+    optional custom vibronic densities n_vib (float64; selects the density populations)."""
     E: torch.Tensor
     g: torch.Tensor
     E_vib: torch.Tensor | None = None
+    n_vib: torch.Tensor | None = None
 
     def c(self):
         _dev(self.E, torch.float64, "E"); _dev(self.g, torch.int32, "g"); _dev(self.E_vib, torch.float64, "E_vib")
-        return pxc_states(_ptr(self.E), _ptr(self.g), _ptr(self.E_vib), self.E.numel())
+        _dev(self.n_vib, torch.float64, "n_vib")
+        return pxc_states(_ptr(self.E), _ptr(self.g), _ptr(self.E_vib), self.E.numel(), _ptr(self.n_vib))
 
 
 @dataclass
@@ -268,6 +275,10 @@ class Workspace:
     def set_accumulate(self, on: bool):
         _check(load().pxc_set_accumulate(self.h, int(on)))
 
+    def set_emission(self, on: bool):
+        """Emission intensities / emission cross sections instead of absorption (workspace mode)."""
+        _check(load().pxc_set_emission(self.h, int(on)))
+
     def set_tile(self, kind: int, batched: bool, tile: int):
         """Profile-kernel tile for this kind and for single-condition (batched=False) or batched calls."""
         _check(load().pxc_set_tile(self.h, int(kind), int(bool(batched)), int(tile)))
@@ -332,6 +343,17 @@ def pxc_cross_section(ws: Workspace, states: States, trans: Transitions, conds, 
     _check(load().pxc_cross_section(ws.h, ctypes.byref(st), ctypes.byref(tr), arr, n_c, ctypes.byref(g),
                                     ctypes.byref(pa), threshold, _ptr(sigma), _ptr(sigma_exp), _stream(stream)))
     return sigma, sigma_exp
+
+
+def pxc_cooling_function(ws: Workspace, states: States, trans: Transitions, conds, stream=None):
+    """(W[n_c], Q[n_c]) float64 on the device: cooling functions, Eq. (cf)."""
+    arr, n_c = _conds(conds)
+    W = torch.empty(n_c, dtype=torch.float64, device="cuda")
+    Q = torch.empty(n_c, dtype=torch.float64, device="cuda")
+    st, tr = states.c(), trans.c()
+    _check(load().pxc_cooling_function(ws.h, ctypes.byref(st), ctypes.byref(tr), arr, n_c, _ptr(W), _ptr(Q),
+                                       _stream(stream)))
+    return W, Q
 
 
 def pxc_autotune(ws: Workspace, states: States, trans: Transitions, conds, grid, profile: Profile,

@@ -22,8 +22,11 @@ struct SlotP {                    // one temperature pair
   double T, T_vib;                // T (T_rot) and T_vib (0 for LTE)
 };
 
+// Partial sums per (block, slot): Q, and the moments for dQ/dT, dQ/dT_vib and the cooling function.
+constexpr int kQMoments = 4;
 void launch_boltzmann(const pxc_states* st, const SlotP* slots_dev, int nslot, double2* srec, int64_t srec_stride,
-                      StateFast* sfast, double* qpart, double* qres, unsigned* err, cudaStream_t s);
+                      StateFast* sfast, double* qpart, double* qres, unsigned* err, cudaStream_t s,
+                      const double* Ssum = nullptr, double* W_out = nullptr);
 
 // Per-state 16-bit energy codes for the intensity pass's prefilter: q = floor((E - Emin) inv_res)
 // for finite E (q <= kCodeMax), kCodeNone otherwise.  For every finite E, Emin + (q - 1) / inv_res
@@ -42,13 +45,41 @@ struct QuantHdr {
 };
 // Three reduction words (ordered keys of -Emin and Emax, max g) followed by the header.
 constexpr int kQuantWords = 4;
+void launch_cool_rates(const pxc_transitions* tr, const pxc_states* st, double* S, unsigned* err, cudaStream_t s);
 void launch_state_codes(const pxc_states* st, code_t* code, unsigned long long* words, cudaStream_t s);
+
+// How a line's value is formed from the per-state population factors b (value = num / den):
+//   IMODE_ABS          absorption, LTE or two temperatures: g' A (b_l - b_u) / (8 pi c Q nu^2)
+//                      (Eqs. abs intensity lte, nlte ab 2T)
+//   IMODE_ABS_DENSITY  absorption, vibronic densities: g' A b_l (1 - exp(-c2 nu / T_rot)) /
+//                      (8 pi c Q nu^2) (Eq. nlte ab pop density)
+//   IMODE_EMISSION     emission, any population model: g' h c A nu b_u / (4 pi Q)
+//                      (Eqs. ems intensity lte, nlte em 2T, nlte em pop density)
+// invQ is 1/(8 pi c Q); h c / (4 pi Q) = 2 h c^2 invQ.
+enum { IMODE_ABS = 0, IMODE_ABS_DENSITY = 1, IMODE_EMISSION = 2 };
+constexpr double kTwoHC2 = 2.0 * kH * kC * kC;
+
+__device__ __forceinline__ void line_value(int mode, double c2_T, double g, double A, double invQ, double bl,
+                                           double bu, double nu, double* num, double* den) {
+  if (mode == IMODE_EMISSION) {
+    *num = g * A * invQ * (kTwoHC2 * bu * nu);
+    *den = 1.0;
+  } else if (mode == IMODE_ABS_DENSITY) {
+    *num = g * A * invQ * (bl * -expm1(-c2_T * nu));
+    *den = nu * nu;
+  } else {
+    *num = g * A * invQ * (bl - bu);
+    *den = nu * nu;
+  }
+}
 
 struct BoundP {
   float log2_thr;
   float log2_invQ;
   float c2_T;
   int lte;
+  int mode;      // IMODE_*
+  double c2_Td;  // c2 / T (T_rot), FP64
 };
 void launch_lines_compact(const pxc_transitions* tr, int64_t ns, const code_t* code, const QuantHdr* qh,
                           const StateFast* sfast, const double2* srec,
@@ -59,7 +90,8 @@ void launch_compact_staged(const uint64_t* kstage, const uint32_t* istage, const
                            uint64_t* okey, uint32_t* oidx, cudaStream_t s);
 
 void launch_lines(const pxc_transitions* tr, const int32_t* g, int64_t ns, const double2* srec,
-                  const double* qres, const GridP& gp, int use_grid, double threshold, int with_intensity,
+                  const double* qres, const GridP& gp, const BoundP& bp, int use_grid, double threshold,
+                  int with_intensity,
                   uint64_t* key, double* Iv, double* nu_out, uint32_t* bcount, int64_t nblk,
                   unsigned long long* maxbits, unsigned* err, cudaStream_t s);
 
@@ -84,7 +116,8 @@ void launch_prepare(const uint64_t* skey, const uint32_t* sidx, const unsigned l
 
 void launch_sorted_intensity(const int32_t* su, const int32_t* sl, const double* sA, const unsigned long long* n_dev,
                              int64_t n_max, const int32_t* g, const double2* srec, const double* qres,
-                             double threshold, double* sI, unsigned long long* maxbits, cudaStream_t s);
+                             const BoundP& bp, double threshold, double* sI, unsigned long long* maxbits,
+                             cudaStream_t s);
 
 void launch_scale(const double* sI, const unsigned long long* n_dev, int64_t n_max, const int32_t* kexp,
                   float* Is, unsigned long long* counters, cudaStream_t s);

@@ -43,19 +43,23 @@ __device__ __forceinline__ T warp_sum(T v) {
 }
 
 // ------------------------------------------------------------------ K-Q: Boltzmann table and Q
-// b_s = exp(-c2 E_s / T) (LTE, Eq. pf) or exp(-c2 E_vib/T_vib - c2 E_rot/T_rot) (Eq. Q nlte 2T);
-// per-block partial sums of g b, g b c2 E_rot / T^2, g b c2 E_vib / T_vib^2 in a fixed order.
+// b_s = exp(-c2 E_s / T) (LTE, Eq. pf), exp(-c2 E_vib/T_vib - c2 E_rot/T_rot) (Eq. Q nlte 2T) or
+// n_vib exp(-c2 E_rot / T_rot) (vibronic densities, Eq. Q nlte Nvib); per-block partial sums of
+// g b, g b c2 E_rot / T, g b c2 E_vib / T_vib and (cooling function) g b S in a fixed order.
 __global__ void __launch_bounds__(kThreadsQ) k_boltzmann(const double* __restrict__ E, const int32_t* __restrict__ g,
-                                                         const double* __restrict__ Ev, int64_t n,
+                                                         const double* __restrict__ Ev,
+                                                         const double* __restrict__ nvib, int64_t n,
                                                          const SlotP* __restrict__ slots, int nslot,
                                                          double2* __restrict__ srec, int64_t stride,
                                                          StateFast* __restrict__ sfast,
+                                                         const double* __restrict__ Ssum,
                                                          double* __restrict__ qpart, unsigned* err) {
-  __shared__ double red[kThreadsQ / 32][3];
+  __shared__ double red[kThreadsQ / 32][kQMoments];
   for (int sl = 0; sl < nslot; ++sl) {
     const SlotP sp = slots[sl];
     const bool two_t = sp.c2_Tv > 0.0;
-    double q0 = 0.0, q1 = 0.0, q2 = 0.0;
+    const bool dens = !two_t && nvib != nullptr;
+    double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;
     unsigned bad = 0;
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
       double e = E[s];
@@ -65,24 +69,33 @@ __global__ void __launch_bounds__(kThreadsQ) k_boltzmann(const double* __restric
       } else if (isinf(e)) {
         bad |= ERRB_NONFINITE;
       } else {
-        double x, er = e, ev = 0.0;
-        if (two_t) {
+        double x, er = e, ev = 0.0, w = 1.0;
+        if (two_t || dens) {
           ev = Ev[s];
           er = e - ev;
           if (!isfinite(ev)) bad |= ERRB_NONFINITE;
+        }
+        if (two_t) {
           x = -(ev * sp.c2_Tv) - er * sp.c2_T;
+        } else if (dens) {
+          // Eq. (F nlte Nvib): n_vib exp(-c2 E_rot / T_rot)
+          w = nvib[s];
+          if (!isfinite(w)) bad |= ERRB_NONFINITE;
+          x = -er * sp.c2_T;
         } else {
           x = -e * sp.c2_T;
         }
         if (x > kExpMax) {
           bad |= ERRB_OVERFLOW;
         } else {
-          b = exp(x);
+          b = w * exp(x);
           lb = x * 1.4426950408889634;
+          if (dens) lb += log2(w);
           double term = (double)g[s] * b;
           q0 += term;
           q1 += term * er * sp.c2_T;   // divided by T in k_qfinal: dQ/dT = sum g b c2 E_rot / T^2
-          q2 += term * ev * sp.c2_Tv;  // divided by T_vib: dQ/dT_vib
+          q2 += term * ev * sp.c2_Tv;  // divided by T_vib: dQ/dT_vib (0 unless two temperatures)
+          if (Ssum) q3 += term * Ssum[s];
         }
       }
       if (srec) srec[(int64_t)sl * stride + s] = make_double2(e, b);
@@ -95,52 +108,88 @@ __global__ void __launch_bounds__(kThreadsQ) k_boltzmann(const double* __restric
       }
     }
     if (bad) set_err(err, bad);
-    // moments: dQ/dT = sum term c2 E_rot / T^2 = (sum term E_rot c2/T) / T
-    q1 = warp_sum(q1); q0 = warp_sum(q0); q2 = warp_sum(q2);
+    q1 = warp_sum(q1); q0 = warp_sum(q0); q2 = warp_sum(q2); q3 = warp_sum(q3);
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) { red[w][0] = q0; red[w][1] = q1; red[w][2] = q2; }
+    if (lane == 0) { red[w][0] = q0; red[w][1] = q1; red[w][2] = q2; red[w][3] = q3; }
     __syncthreads();
     if (threadIdx.x == 0) {
-      double a0 = 0, a1 = 0, a2 = 0;
-      for (int i = 0; i < kThreadsQ / 32; ++i) { a0 += red[i][0]; a1 += red[i][1]; a2 += red[i][2]; }
-      double* o = qpart + ((int64_t)blockIdx.x * nslot + sl) * 3;
-      o[0] = a0; o[1] = a1; o[2] = a2;
+      double a[kQMoments] = {0.0, 0.0, 0.0, 0.0};
+      for (int i = 0; i < kThreadsQ / 32; ++i)
+        for (int m = 0; m < kQMoments; ++m) a[m] += red[i][m];
+      double* o = qpart + ((int64_t)blockIdx.x * nslot + sl) * kQMoments;
+      for (int m = 0; m < kQMoments; ++m) o[m] = a[m];
     }
     __syncthreads();
   }
 }
 
+// qres[sl] = {Q, dQ/dT (or dQ/dT_rot), dQ/dT_vib, 1/(8 pi c Q)}; W_out[sl] (if given) =
+// (h c / 4 pi Q) sum_s g_s b_s S_s, the cooling function of Eq. (cf).
 __global__ void k_qfinal(const double* __restrict__ qpart, int nblk, int nslot, const SlotP* __restrict__ slots,
-                         double* __restrict__ qres) {
-  __shared__ double red[32][3];
+                         double* __restrict__ qres, double* __restrict__ W_out) {
+  __shared__ double red[32][kQMoments];
   int sl = blockIdx.x;
-  double a0 = 0, a1 = 0, a2 = 0;
+  double a[kQMoments] = {0.0, 0.0, 0.0, 0.0};
   for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
-    const double* o = qpart + ((int64_t)b * nslot + sl) * 3;
-    a0 += o[0]; a1 += o[1]; a2 += o[2];
+    const double* o = qpart + ((int64_t)b * nslot + sl) * kQMoments;
+    for (int m = 0; m < kQMoments; ++m) a[m] += o[m];
   }
-  a0 = warp_sum(a0); a1 = warp_sum(a1); a2 = warp_sum(a2);
+  for (int m = 0; m < kQMoments; ++m) a[m] = warp_sum(a[m]);
   int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) { red[w][0] = a0; red[w][1] = a1; red[w][2] = a2; }
+  if (lane == 0)
+    for (int m = 0; m < kQMoments; ++m) red[w][m] = a[m];
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s0 = 0, s1 = 0, s2 = 0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { s0 += red[i][0]; s1 += red[i][1]; s2 += red[i][2]; }
+    double t[kQMoments] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i)
+      for (int m = 0; m < kQMoments; ++m) t[m] += red[i][m];
     const SlotP sp = slots[sl];
     double* r = qres + sl * 4;
-    r[0] = s0;
-    r[1] = s1 / sp.T;                                 // dQ/dT (or dQ/dT_rot)
-    r[2] = sp.c2_Tv > 0.0 ? s2 / sp.T_vib : 0.0;      // dQ/dT_vib
-    r[3] = 1.0 / (8.0 * kPi * kC * s0);
+    r[0] = t[0];
+    r[1] = t[1] / sp.T;                                 // dQ/dT (or dQ/dT_rot)
+    r[2] = sp.c2_Tv > 0.0 ? t[2] / sp.T_vib : 0.0;      // dQ/dT_vib
+    r[3] = 1.0 / (8.0 * kPi * kC * t[0]);
+    if (W_out) W_out[sl] = kH * kC * t[3] / (4.0 * kPi * t[0]);
   }
 }
 
 void launch_boltzmann(const pxc_states* st, const SlotP* slots_dev, int nslot, double2* srec, int64_t srec_stride,
-                      StateFast* sfast, double* qpart, double* qres, unsigned* err, cudaStream_t s) {
-  k_boltzmann<<<kQBlocks, kThreadsQ, 0, s>>>(st->E, st->g, st->E_vib, st->n, slots_dev, nslot, srec, srec_stride,
-                                             sfast, qpart, err);
-  k_qfinal<<<nslot, 1024, 0, s>>>(qpart, kQBlocks, nslot, slots_dev, qres);
+                      StateFast* sfast, double* qpart, double* qres, unsigned* err, cudaStream_t s,
+                      const double* Ssum, double* W_out) {
+  k_boltzmann<<<kQBlocks, kThreadsQ, 0, s>>>(st->E, st->g, st->E_vib, st->n_vib, st->n, slots_dev, nslot, srec,
+                                             srec_stride, sfast, Ssum, qpart, err);
+  k_qfinal<<<nslot, 1024, 0, s>>>(qpart, kQBlocks, nslot, slots_dev, qres, W_out);
   note_launches(2);
+}
+
+// ------------------------------------------------------------------ cooling function: per-state rates
+// S[u] += A nu over every line u -> l with nu = E[u] - E[l] > 0 (FP64 atomics; the order of the
+// additions, and so the last bits of S, depends on scheduling).  With them the cooling function of
+// Eq. (cf) is W = (h c / 4 pi Q) sum_u g_u b_u S_u, one more moment of the state pass.
+__global__ void __launch_bounds__(256) k_cool_rates(const int32_t* __restrict__ up, const int32_t* __restrict__ lo,
+                                                    const void* __restrict__ Av, int A32, int64_t n,
+                                                    const double* __restrict__ E, int64_t ns,
+                                                    double* __restrict__ S, unsigned* err) {
+  unsigned bad = 0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = __ldcs(up + t), l = __ldcs(lo + t);
+    const double A = A32 ? (double)__ldcs((const float*)Av + t) : __ldcs((const double*)Av + t);
+    if (u < 0 || u >= ns || l < 0 || l >= ns) { bad |= ERRB_ID; continue; }
+    if (!isfinite(A)) { bad |= ERRB_NONFINITE; continue; }
+    const double nu = __dsub_rn(E[u], E[l]);
+    if (nu > 0.0) atomicAdd(S + u, A * nu);
+  }
+  if (bad) set_err(err, bad);
+}
+
+void launch_cool_rates(const pxc_transitions* tr, const pxc_states* st, double* S, unsigned* err, cudaStream_t s) {
+  cudaMemsetAsync(S, 0, sizeof(double) * (size_t)(st->n > 0 ? st->n : 1), s);
+  if (tr->n == 0) return;
+  int64_t blocks = (tr->n + 255) / 256;
+  if (blocks > 148 * 16) blocks = 148 * 16;
+  k_cool_rates<<<(unsigned)blocks, 256, 0, s>>>(tr->upper, tr->lower, tr->A, tr->A_is_f32, tr->n, st->E, st->n, S,
+                                                err);
+  note_launches(1);
 }
 
 // ------------------------------------------------------------------ per-state energy codes
@@ -240,7 +289,7 @@ __global__ void __launch_bounds__(kThreadsI) k_lines(const int32_t* __restrict__
                                                      const void* __restrict__ Av, int A32, int64_t n,
                                                      const double2* __restrict__ srec, const int32_t* __restrict__ g,
                                                      int64_t ns, const double* __restrict__ qres, GridP gp,
-                                                     int use_grid, double threshold, int with_I,
+                                                     BoundP bp, int use_grid, double threshold, int with_I,
                                                      uint64_t* __restrict__ key, double* __restrict__ Iv,
                                                      double* __restrict__ nu_out, uint32_t* __restrict__ bcount,
                                                      unsigned long long* __restrict__ maxbits, unsigned* err) {
@@ -269,9 +318,9 @@ __global__ void __launch_bounds__(kThreadsI) k_lines(const int32_t* __restrict__
       bool keep = nu > 0.0;
       if (keep && use_grid) keep = window_meets_grid(nu, gp);
       if (keep && with_I) {
-        // |I| >= threshold tested as |num| >= threshold * nu^2 (no division for dropped lines)
-        const double num = (double)g[u] * A * invQ * (rl.y - ru.y);
-        const double den = nu * nu;
+        // |I| >= threshold tested as |num| >= threshold * den (no division for dropped lines)
+        double num, den;
+        line_value(bp.mode, bp.c2_Td, (double)g[u], A, invQ, rl.y, ru.y, nu, &num, &den);
         keep = fabs(num) >= threshold * den;
         if (keep) I = num / den;
       }
@@ -308,12 +357,13 @@ __global__ void __launch_bounds__(kThreadsI) k_lines(const int32_t* __restrict__
 }
 
 void launch_lines(const pxc_transitions* tr, const int32_t* g, int64_t ns, const double2* srec,
-                  const double* qres, const GridP& gp, int use_grid, double threshold, int with_intensity,
+                  const double* qres, const GridP& gp, const BoundP& bp, int use_grid, double threshold,
+                  int with_intensity,
                   uint64_t* key, double* Iv, double* nu_out, uint32_t* bcount, int64_t nblk,
                   unsigned long long* maxbits, unsigned* err, cudaStream_t s) {
   if (nblk == 0) return;
   k_lines<<<(unsigned)nblk, kThreadsI, 0, s>>>(tr->upper, tr->lower, tr->A, tr->A_is_f32, tr->n, srec, g, ns, qres,
-                                               gp, use_grid, threshold, with_intensity, key, Iv, nu_out, bcount,
+                                               gp, bp, use_grid, threshold, with_intensity, key, Iv, nu_out, bcount,
                                                maxbits, err);
   note_launches(1);
 }
@@ -396,7 +446,8 @@ __global__ void __launch_bounds__(kThreadsI) k_lines_c(const int32_t* __restrict
     // the codes are used when their resolution is at most 1/16 of the kept nu range (a list
     // whose energies span far more than the window gains nothing from them)
     c.pre = code != nullptr && qh.enabled && (wh - wl) * qh.inv_res >= 16.0;
-    c.pre_thr = c.pre && with_I && threshold > 0.0 && bp.lte;
+    // the code bound on b_l holds for LTE absorption only
+    c.pre_thr = c.pre && with_I && threshold > 0.0 && bp.lte && bp.mode == IMODE_ABS;
     c.dlo = INT_MIN;
     c.dhi = INT_MAX;
     if (c.pre) {
@@ -451,14 +502,22 @@ __global__ void __launch_bounds__(kThreadsI) k_lines_c(const int32_t* __restrict
       }
       if (keep && with_I) {
         if (threshold > 0.0) {
+          // conservative FP32 log2 bound on |value| (see line_value)
           const float nuf = (float)nu;
-          const float m = bp.lte ? fminf(1.f, bp.c2_T * nuf) : 1.f;
-          const float P = (float)fu.g * (float)A * m / (nuf * nuf);
-          if (__log2f(P) + fmaxf(fu.lb, fl.lb) + c.l2invQ < bp.log2_thr) keep = false;
+          float P, lbb;
+          if (bp.mode == IMODE_EMISSION) {
+            P = (float)fu.g * (float)A * nuf * (float)kTwoHC2;
+            lbb = fu.lb;
+          } else {
+            const float m = bp.lte ? fminf(1.f, bp.c2_T * nuf) : 1.f;
+            P = (float)fu.g * (float)A * m / (nuf * nuf);
+            lbb = fmaxf(fu.lb, fl.lb);
+          }
+          if (__log2f(P) + lbb + c.l2invQ < bp.log2_thr) keep = false;
         }
         if (keep) {
-          const double num = (double)fu.g * A * c.invQ * (srec[l].y - srec[u].y);
-          const double den = nu * nu;
+          double num, den;
+          line_value(bp.mode, bp.c2_Td, (double)fu.g, A, c.invQ, srec[l].y, srec[u].y, nu, &num, &den);
           keep = fabs(num) >= threshold * den;
           if (keep) I = num / den;
         }
@@ -881,8 +940,8 @@ __global__ void __launch_bounds__(256) k_sorted_intensity(const int32_t* __restr
                                                           const unsigned long long* __restrict__ n_dev,
                                                           const int32_t* __restrict__ g,
                                                           const double2* __restrict__ srec,
-                                                          const double* __restrict__ qres, double threshold,
-                                                          double* __restrict__ sI,
+                                                          const double* __restrict__ qres, BoundP bp,
+                                                          double threshold, double* __restrict__ sI,
                                                           unsigned long long* __restrict__ maxbits) {
   const int64_t n = (int64_t)*n_dev;
   const double invQ = qres[3];
@@ -891,8 +950,8 @@ __global__ void __launch_bounds__(256) k_sorted_intensity(const int32_t* __restr
     int32_t u = su[j], l = sl[j];
     double2 ru = srec[u], rl = srec[l];
     double nu = __dsub_rn(ru.x, rl.x);
-    const double num = (double)g[u] * sA[j] * invQ * (rl.y - ru.y);
-    const double den = nu * nu;
+    double num, den;
+    line_value(bp.mode, bp.c2_Td, (double)g[u], sA[j], invQ, rl.y, ru.y, nu, &num, &den);
     double I = fabs(num) >= threshold * den ? num / den : 0.0;
     sI[j] = I;
     unsigned long long ib = (unsigned long long)__double_as_longlong(fabs(I));
@@ -908,11 +967,12 @@ __global__ void __launch_bounds__(256) k_sorted_intensity(const int32_t* __restr
 
 void launch_sorted_intensity(const int32_t* su, const int32_t* sl, const double* sA, const unsigned long long* n_dev,
                              int64_t n_max, const int32_t* g, const double2* srec, const double* qres,
-                             double threshold, double* sI, unsigned long long* maxbits, cudaStream_t s) {
+                             const BoundP& bp, double threshold, double* sI, unsigned long long* maxbits,
+                             cudaStream_t s) {
   if (n_max == 0) return;
   int64_t blocks = (n_max + 255) / 256;
   if (blocks > 148 * 16) blocks = 148 * 16;
-  k_sorted_intensity<<<(unsigned)blocks, 256, 0, s>>>(su, sl, sA, n_dev, g, srec, qres, threshold, sI, maxbits);
+  k_sorted_intensity<<<(unsigned)blocks, 256, 0, s>>>(su, sl, sA, n_dev, g, srec, qres, bp, threshold, sI, maxbits);
   note_launches(1);
 }
 

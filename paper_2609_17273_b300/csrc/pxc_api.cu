@@ -65,7 +65,7 @@ Layout make_layout(const pxc_capacity& c) {
   auto take = [&](size_t bytes) { size_t r = o; o += al(bytes); return r; };
   L.err = take(256);
   L.counters = take(CNT_N * 8);
-  L.qpart = take((size_t)kQBlocks * L.max_cond * 3 * 8);
+  L.qpart = take((size_t)kQBlocks * L.max_cond * kQMoments * 8);
   L.qres = take((size_t)L.max_cond * 4 * 8);
   L.slots = take((size_t)L.max_cond * sizeof(SlotP));
   L.cond = take((size_t)L.max_cond * sizeof(CondDev));
@@ -118,6 +118,9 @@ pxc_status check_cond(const pxc_condition& c, bool need_vib, const pxc_states* s
   if (!(c.T > 0.0) || !std::isfinite(c.T)) return fail(PXC_ERR_ARG, "condition: T must be > 0");
   if (!std::isfinite(c.T_vib)) return fail(PXC_ERR_ARG, "condition: T_vib not finite");
   if (c.T_vib > 0.0 && (!st || bad_ptr(st->E_vib))) return fail(PXC_ERR_ARG, "condition: T_vib > 0 needs E_vib");
+  if (st && st->n_vib && bad_ptr(st->E_vib)) return fail(PXC_ERR_ARG, "states: vibronic densities need E_vib");
+  if (st && st->n_vib && c.T_vib > 0.0)
+    return fail(PXC_ERR_ARG, "condition: T_vib > 0 with vibronic densities is ambiguous");
   (void)need_vib;
   return PXC_OK;
 }
@@ -180,6 +183,8 @@ struct WsExtra {
   cudaStream_t copy_stream;
   cudaEvent_t ev_copied[2], ev_done[2];
   int occ[4][kNumTiles];  // resident profile CTAs per SM for each kind and tile
+  int emission;           // emission intensities instead of absorption
+  const double* cache_nvib;  // densities the cached Boltzmann table was built with
   int tile[4][2];         // tile used for each kind, [single condition, batched]
   // last call
   int64_t last_nseg;
@@ -260,7 +265,7 @@ void run_boltzmann(pxc_workspace* ws, const pxc_states* st, const pxc_condition&
                    bool allow_cache) {
   WsExtra* x = X(ws);
   if (allow_cache && ws->cache_valid && ws->cache_E == st->E && ws->cache_n == st->n && ws->cache_T == c.T &&
-      ws->cache_Tv == c.T_vib)
+      ws->cache_Tv == c.T_vib && x->cache_nvib == st->n_vib)
     return;
   SlotP sp = make_slot(c);
   SlotP* dslot = at<SlotP>(ws, x->L.slots) + slot;
@@ -271,18 +276,21 @@ void run_boltzmann(pxc_workspace* ws, const pxc_states* st, const pxc_condition&
   if (slot == 0) launch_state_codes(st, at<code_t>(ws, x->L.code), at<unsigned long long>(ws, x->L.qwords), s);
   ws->cache_valid = allow_cache ? 1 : 0;
   ws->cache_E = st->E; ws->cache_n = st->n; ws->cache_T = c.T; ws->cache_Tv = c.T_vib;
+  x->cache_nvib = st->n_vib;
 }
 
 const QuantHdr* qhdr(pxc_workspace* ws) {
   return reinterpret_cast<const QuantHdr*>(at<unsigned long long>(ws, X(ws)->L.qwords) + kQuantWords);
 }
 
-BoundP make_bound(const pxc_condition& c, double threshold) {
+BoundP make_bound(pxc_workspace* ws, const pxc_states* st, const pxc_condition& c, double threshold) {
   BoundP bp{};
   bp.log2_thr = threshold > 0.0 ? (float)(std::log2(threshold) - 1e-3) : -INFINITY;
   bp.log2_invQ = 0.f;
   bp.lte = c.T_vib > 0.0 ? 0 : 1;
-  bp.c2_T = (float)(kH * kC / kKB / c.T);
+  bp.c2_Td = kH * kC / kKB / c.T;
+  bp.c2_T = (float)bp.c2_Td;
+  bp.mode = X(ws)->emission ? IMODE_EMISSION : (st->n_vib ? IMODE_ABS_DENSITY : IMODE_ABS);
   return bp;
 }
 
@@ -297,7 +305,7 @@ pxc_status front_plain(pxc_workspace* ws, const pxc_states* st, const pxc_transi
   cudaMemsetAsync(at<unsigned long long>(ws, L.maxbits), 0, 8, s);
   const int64_t nunit = (tr->n + kUnitLines - 1) / kUnitLines;
   tmark(ws, 0, true, s);
-  BoundP bp = make_bound(c, threshold);
+  BoundP bp = make_bound(ws, st, c, threshold);
   launch_lines_compact(tr, st->n, at<code_t>(ws, L.code), qhdr(ws), at<StateFast>(ws, L.sfast),
                        at<double2>(ws, L.srec), at<double>(ws, L.qres), gp, threshold, bp, 1, at<uint64_t>(ws, L.key),
                        at<uint32_t>(ws, L.sidx1), at<double>(ws, L.Iv), at<uint32_t>(ws, L.bcount), nunit,
@@ -413,6 +421,12 @@ pxc_status pxc_workspace_destroy(pxc_workspace* ws) {
   return PXC_OK;
 }
 
+pxc_status pxc_set_emission(pxc_workspace* ws, int on) {
+  if (!ws) return fail(PXC_ERR_ARG, "set_emission: null workspace");
+  X(ws)->emission = on ? 1 : 0;
+  return PXC_OK;
+}
+
 pxc_status pxc_set_accumulate(pxc_workspace* ws, int on) {
   if (!ws) return fail(PXC_ERR_ARG, "null workspace");
   ws->accumulate = on ? 1 : 0;
@@ -463,6 +477,34 @@ pxc_status pxc_partition_function(pxc_workspace* ws, const pxc_states* st, const
   return cuda_check("partition_function");
 }
 
+pxc_status pxc_cooling_function(pxc_workspace* ws, const pxc_states* st, const pxc_transitions* tr,
+                                const pxc_condition* c, int32_t n_c, double* W_out, double* Q_out, cudaStream_t s) {
+  if (!ws || !c || n_c < 1 || !W_out) return fail(PXC_ERR_ARG, "cooling_function: bad arguments");
+  pxc_status r;
+  if ((r = check_states(st)) || (r = check_trans(tr))) return r;
+  WsExtra* x = X(ws);
+  if (n_c > x->L.max_cond) return fail(PXC_ERR_CAPACITY, "cooling_function: n_c above capacity");
+  if (tr->n > ws->cap.max_lines || st->n > ws->cap.max_states)
+    return fail(PXC_ERR_CAPACITY, "cooling_function: above workspace capacity");
+  std::vector<SlotP> sp(n_c);
+  for (int i = 0; i < n_c; ++i) {
+    if ((r = check_cond(c[i], false, st))) return r;
+    sp[i] = make_slot(c[i]);
+  }
+  SlotP* dslot = at<SlotP>(ws, x->L.slots);
+  if ((r = upload(ws, dslot, sp.data(), sizeof(SlotP) * n_c, s))) return r;
+  // the per-state rates S reuse the Boltzmann-table region (8 of its 16 bytes per state)
+  double* S = at<double>(ws, x->L.srec);
+  ws->cache_valid = 0;
+  launch_cool_rates(tr, st, S, ws->err, s);
+  double* qres = at<double>(ws, x->L.qres);
+  launch_boltzmann(st, dslot, n_c, nullptr, 0, nullptr, at<double>(ws, x->L.qpart), qres, ws->err, s, S, W_out);
+  if (Q_out)
+    for (int i = 0; i < n_c; ++i) cudaMemcpyAsync(Q_out + i, qres + 4 * i, 8, cudaMemcpyDeviceToDevice, s);
+  x->last_nseg = 0;
+  return cuda_check("cooling_function");
+}
+
 pxc_status pxc_line_intensities(pxc_workspace* ws, const pxc_states* st, const pxc_transitions* tr,
                                 const pxc_condition* c, const pxc_grid* grid, double cutoff, double threshold,
                                 double* nu_out, float* I_scaled_out, int32_t* I_exp_out, int64_t* n_kept_out,
@@ -482,7 +524,8 @@ pxc_status pxc_line_intensities(pxc_workspace* ws, const pxc_states* st, const p
   run_boltzmann(ws, st, *c, 0, s, false);
   cudaMemsetAsync(at<unsigned long long>(ws, L.maxbits), 0, 8, s);
   const int64_t nblk = (tr->n + kLinesPerBlockI - 1) / kLinesPerBlockI;
-  launch_lines(tr, st->g, st->n, at<double2>(ws, L.srec), at<double>(ws, L.qres), gp, grid ? 1 : 0, threshold, 1,
+  const BoundP bp = make_bound(ws, st, *c, threshold);
+  launch_lines(tr, st->g, st->n, at<double2>(ws, L.srec), at<double>(ws, L.qres), gp, bp, grid ? 1 : 0, threshold, 1,
                at<uint64_t>(ws, L.key), at<double>(ws, L.Iv), nu_out, at<uint32_t>(ws, L.bcount), nblk,
                at<unsigned long long>(ws, L.maxbits), ws->err, s);
   if (nblk) launch_scan_counts(at<uint32_t>(ws, L.bcount), nblk, cnt + CNT_KEPT, s);
@@ -555,7 +598,7 @@ pxc_status pxc_cross_section(pxc_workspace* ws, const pxc_states* st, const pxc_
     // The geometry pass reads E through the state table, so fill it (first slot) first.
     run_boltzmann(ws, st, slots[0], 0, s, false);
     const int64_t nunit = (tr->n + kUnitLines - 1) / kUnitLines;
-    BoundP bp = make_bound(c[0], 0.0);
+    BoundP bp = make_bound(ws, st, c[0], 0.0);
     launch_lines_compact(tr, st->n, at<code_t>(ws, L.code), qhdr(ws), at<StateFast>(ws, L.sfast),
                          at<double2>(ws, L.srec), at<double>(ws, L.qres), gp, 0.0, bp, 0, at<uint64_t>(ws, L.key),
                          idxs[1], nullptr, at<uint32_t>(ws, L.bcount), nunit, nullptr, ws->err, s);
@@ -569,8 +612,9 @@ pxc_status pxc_cross_section(pxc_workspace* ws, const pxc_states* st, const pxc_
       if (k) run_boltzmann(ws, st, slots[k], (int)k, s, false);
       cudaMemsetAsync(at<unsigned long long>(ws, L.maxbits) + k, 0, 8, s);
       launch_sorted_intensity(at<int32_t>(ws, L.su), at<int32_t>(ws, L.sl), at<double>(ws, L.sA), cnt + CNT_KEPT,
-                              tr->n, st->g, at<double2>(ws, L.srec), at<double>(ws, L.qres) + 4 * k, threshold,
-                              at<double>(ws, L.sI), at<unsigned long long>(ws, L.maxbits) + k, s);
+                              tr->n, st->g, at<double2>(ws, L.srec), at<double>(ws, L.qres) + 4 * k,
+                              make_bound(ws, st, slots[k], threshold), threshold, at<double>(ws, L.sI),
+                              at<unsigned long long>(ws, L.maxbits) + k, s);
       launch_exponent(at<unsigned long long>(ws, L.maxbits) + k, kexp + 2 * k, nullptr, 0, nullptr, 0, s);
       launch_scale(at<double>(ws, L.sI), cnt + CNT_KEPT, tr->n, kexp + 2 * k,
                    at<float>(ws, L.Is) + (int64_t)k * L.is_stride, cnt, s);
@@ -628,6 +672,8 @@ pxc_status pxc_cross_section_backward(pxc_workspace* ws, const pxc_states* st, c
   if (tr->n > ws->cap.max_lines || st->n > ws->cap.max_states || grid->n > std::max<int64_t>(ws->cap.max_grid, 1))
     return fail(PXC_ERR_CAPACITY, "backward: above workspace capacity");
   if (ws->accumulate) return fail(PXC_ERR_ARG, "backward: accumulate mode is forward-only");
+  if (x->emission || st->n_vib)
+    return fail(PXC_ERR_ARG, "backward: absorption with LTE or two-temperature populations only");
   GridP gp = make_gridp(*grid, pa->cutoff);
   unsigned long long* cnt = at<unsigned long long>(ws, L.counters);
   cudaMemsetAsync(cnt, 0, CNT_N * 8, s);

@@ -29,9 +29,9 @@ namespace {
 constexpr int kNoAllocConditions = 64;
 constexpr int kMaxDevices = 64;
 
-// Scratch layout, in doubles: partials [kQBlocks][64][3], results [64][4],
+// Scratch layout, in doubles: partials [kQBlocks][64][kQMoments], results [64][4],
 // condition constants [64] SlotP (4 doubles each), error word.
-constexpr size_t kPartDoubles = (size_t)pxc::kQBlocks * kNoAllocConditions * 3;
+constexpr size_t kPartDoubles = (size_t)pxc::kQBlocks * kNoAllocConditions * pxc::kQMoments;
 constexpr size_t kResDoubles = (size_t)kNoAllocConditions * 4;
 constexpr size_t kSlotDoubles = (size_t)kNoAllocConditions * sizeof(pxc::SlotP) / sizeof(double);
 constexpr size_t kScratchDoubles = kPartDoubles + kResDoubles + kSlotDoubles + 32;
@@ -92,8 +92,10 @@ extern "C" pxc_status pxc_partition_function_noalloc(const pxc_states* states, c
   conds.n = n_c;
   const double c2 = pxc::kH * pxc::kC / pxc::kKB;
   for (int i = 0; i < n_c; ++i) {
-    if (!(c[i].T > 0.0) || (c[i].T_vib > 0.0 && !states->E_vib)) {
-      pxc::set_last_error("partition_function_noalloc: bad condition (T <= 0, or T_vib > 0 without E_vib)");
+    if (!(c[i].T > 0.0) || (c[i].T_vib > 0.0 && !states->E_vib) ||
+        (states->n_vib && (!states->E_vib || c[i].T_vib > 0.0))) {
+      pxc::set_last_error("partition_function_noalloc: bad condition (T <= 0, T_vib > 0 without E_vib, or "
+                          "vibronic densities without E_vib or with T_vib > 0)");
       return PXC_ERR_ARG;
     }
     pxc::SlotP& sp = conds.s[i];

@@ -60,7 +60,7 @@ def _p(a):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
 
 
-ST_GAMMA, ST_NEXP = 4, 5
+ST_GAMMA, ST_NEXP, ST_VIBDENS = 4, 5, 9
 
 
 @dataclass
@@ -135,6 +135,19 @@ class Workload:
         lib.synth_uniform_f32(self.seed, ST_GAMMA, t0, n, self.gamma_range[0], self.gamma_range[1], _p(gr))
         lib.synth_uniform_f32(self.seed, ST_NEXP, t0, n, self.n_range[0], self.n_range[1], _p(ne))
         return gr, ne
+
+    def vib_densities(self) -> np.ndarray:
+        """Per-state custom vibronic densities n_vib[f64] for a diatomic level scheme: one
+        seeded, non-thermal weight per vibrational manifold, (0.5 + U) exp(-v / 2.5), normalised
+        to sum 1 over the manifolds; every rotational state of manifold v carries its weight."""
+        if self.scheme != "diatomic":
+            raise ValueError("vibronic densities are generated for diatomic level schemes")
+        u = np.empty(self.nv, np.float32)
+        _load().synth_uniform_f32(self.seed, ST_VIBDENS, 0, self.nv, 0.0, 1.0, _p(u))
+        v = np.arange(self.nv)
+        w = (0.5 + u.astype(np.float64)) * np.exp(-v / 2.5)
+        w /= w.sum()
+        return np.repeat(w, self.nJ)[: self.n_states].copy()
 
     def weights(self, n: int | None = None, seed_offset: int = 7):
         """Seeded N(0,1) loss weights w(nu) on the grid."""

@@ -28,14 +28,15 @@ def case(name: str, n_trans: int | None = None, n_states: int | None = None, **k
     return {"w": w, "E": E, "g": g, "Ev": Ev, "up": up, "lo": lo, "A": A, "gr": gr, "ne": ne}
 
 
-def oracle_run(c, kind=None, T=None, T_vib=None, P=None, threshold=None, with_sigma=True, literal=False):
+def oracle_run(c, kind=None, T=None, T_vib=None, P=None, threshold=None, with_sigma=True, literal=False,
+               emission=False, n_vib=None):
     w = c["w"]
     return oracle.run(c["E"], c["g"], c["Ev"], c["up"], c["lo"], c["A"], c["gr"], c["ne"],
                       kind=kind or w.profile, T=w.T if T is None else T,
                       T_vib=w.T_vib if T_vib is None else T_vib, P=w.P if P is None else P,
                       mass_da=w.mass_da, hwhm=w.hwhm, nu_min=w.nu_min, dnu=w.dnu, n_grid=w.n_grid,
                       cut=w.cutoff, threshold=w.threshold if threshold is None else threshold,
-                      with_sigma=with_sigma)
+                      with_sigma=with_sigma, emission=emission, n_vib=n_vib)
 
 
 def device(c, kind=None):
