@@ -23,7 +23,8 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "_oracle.so")
 _lib = None
 
-KIND = {"gauss_doppler": 0, "gauss_hwhm": 1, "lorentz": 2, "voigt": 3}
+KIND = {"gauss_doppler": 0, "gauss_hwhm": 1, "lorentz": 2, "voigt": 3,
+        "binned_gauss_doppler": 4, "binned_gauss_hwhm": 5, "binned_lorentz": 6, "binned_voigt": 7}
 STATUS = {0: "ok", 1: "bad argument", 2: "state id out of range", 3: "non-finite input",
           4: "Boltzmann exponent overflow"}
 
@@ -48,6 +49,7 @@ def _load():
         L.orc_faddeeva.argtypes = [i64, P, P, P, P]
         L.orc_profile.argtypes = [cint, i64, P, dbl, dbl, P, P, P]
         L.orc_partition.argtypes = [P, P, P, i64, dbl, dbl, P]
+        L.orc_profile_binned.argtypes = [cint, i64, P, dbl, dbl, dbl, P]
         L.orc_line_intensities.argtypes = [P, P, P, i64, P, P, P, cint, i64, dbl, dbl, dbl,
                                            dbl, dbl, i64, dbl, dbl, P, P, P, P, P]
         L.orc_partition_density.argtypes = [P, P, P, P, i64, dbl, P]
@@ -107,6 +109,15 @@ def profile(kind: str, x, alpha: float, gamma: float = 0.0, derivs: bool = False
     f = np.empty_like(x); fa = np.empty_like(x); fg = np.empty_like(x)
     _load().orc_profile(KIND[kind], x.size, _p(x), alpha, gamma, _p(f), _p(fa), _p(fg))
     return (f, fa, fg) if derivs else f
+
+
+def profile_binned(kind: str, x, dnu: float, alpha: float, gamma: float = 0.0):
+    """Average of the profile `kind` ("gauss_*", "lorentz", "voigt" or their "binned_" names) over
+    the bins [x - dnu/2, x + dnu/2]."""
+    x = _c(np.atleast_1d(x), np.float64)
+    f = np.empty_like(x)
+    _load().orc_profile_binned(KIND[kind.replace("binned_", "")], x.size, _p(x), dnu, alpha, gamma, _p(f))
+    return f
 
 
 def partition(E, g, E_vib=None, T=296.0, T_vib=0.0):

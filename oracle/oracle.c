@@ -19,6 +19,7 @@
  *   I (vibronic density) Eq. (nlte ab pop density)
  *   epsilon (emission)   Eqs. (ems intensity lte), (nlte em 2T), (nlte em pop density)
  *   W(T)                 Eq. (cf), cooling function  [reading R17 below for non-LTE]
+ *   binned profiles      Table (profile), binned Doppler / Gaussian / Lorentzian / Voigt [R19]
  *
  * Readings where the text is silent or garbled (each also listed in the design doc):
  *   R7  nu = E' - E''; lines with nu <= 0 are dropped (nu = 0 would divide by zero).
@@ -35,6 +36,11 @@
  *       with nu > 0 (no grid window, no threshold); Eq. (cf) is its LTE case, and the
  *       non-LTE populations of Eqs. (nlte em 2T) / (nlte em pop density) give the
  *       non-LTE cases.
+ *   R19 a binned profile is the average of the profile over the grid bin centred on the grid
+ *       point, (1/dnu) int_{nu_i - dnu/2}^{nu_i + dnu/2} f(nu - nu_l) dnu; the window (R8) is
+ *       the same as for sampled profiles.  Gaussian: erf/erfc differences; Lorentzian: the
+ *       arctangent difference; Voigt (no closed-form integral): adaptive Gauss-Legendre
+ *       quadrature of the Voigt profile over the bin to 1e-12 relative.
  *   R18 vibronic densities: E_rot = E - E_vib within each manifold, T (the condition's
  *       temperature) is T_rot, and the densities are used as given (every formula is
  *       invariant under a common scale, so normalising them changes nothing).
@@ -75,6 +81,8 @@
 
 enum { ORC_OK = 0, ORC_ERR_ARG = 1, ORC_ERR_ID = 2, ORC_ERR_NONFINITE = 3, ORC_ERR_OVERFLOW = 4 };
 enum { ORC_GAUSS_DOPPLER = 0, ORC_GAUSS_HWHM = 1, ORC_LORENTZ = 2, ORC_VOIGT = 3 };
+/* Binned kinds (Table profile): kind | ORC_BINNED, the widths of the base kind kind & 3. */
+enum { ORC_BINNED = 4 };
 
 double orc_c2(void) { return ORC_H * ORC_C / ORC_KB; }
 
@@ -177,6 +185,96 @@ void orc_profile(int kind, int64_t n, const double* x, double a, double g, doubl
     if (fa) fa[i] = t1;
     if (fg) fg[i] = t2;
   }
+}
+
+/* ---------------------------------------------------------------------------
+ * Binned profiles (R19).  x is the offset of the bin centre from the line centre.
+ * ------------------------------------------------------------------------ */
+
+/* Gauss-Legendre nodes and weights on [-1, 1] by Newton iteration on P_n. */
+static double gl_x[2][16], gl_w[2][16];
+static int gl_ready = 0;
+static void gl_init(void) {
+  const int ns[2] = {8, 16};
+  for (int q = 0; q < 2; ++q) {
+    int n = ns[q];
+    for (int i = 0; i < n; ++i) {
+      double x = cos(ORC_PI * (i + 0.75) / (n + 0.5));
+      for (int it = 0; it < 100; ++it) {
+        double p0 = 1.0, p1 = x;
+        for (int k = 2; k <= n; ++k) { double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k; p0 = p1; p1 = p2; }
+        double dp = n * (x * p1 - p0) / (x * x - 1.0);
+        double dx = p1 / dp;
+        x -= dx;
+        if (fabs(dx) < 1e-16) break;
+      }
+      double p0 = 1.0, p1 = x;
+      for (int k = 2; k <= n; ++k) { double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k; p0 = p1; p1 = p2; }
+      double dp = n * (x * p1 - p0) / (x * x - 1.0);
+      gl_x[q][i] = x;
+      gl_w[q][i] = 2.0 / ((1.0 - x * x) * dp * dp);
+    }
+  }
+  gl_ready = 1;
+}
+
+static double gl_voigt(int q, double a, double b, double alpha, double g) {
+  const int n = q ? 16 : 8;
+  double m = 0.5 * (a + b), h = 0.5 * (b - a), s = 0.0;
+  for (int i = 0; i < n; ++i) s += gl_w[q][i] * prof_voigt(m + h * gl_x[q][i], alpha, g);
+  return s * h;
+}
+
+/* Integral of the Voigt profile over [a, b]: accept the 16-point rule where it agrees with the
+ * 8-point rule to the absolute tolerance tol (1e-13 of the whole bin's first estimate),
+ * otherwise bisect (at most 30 levels). */
+static double adapt_voigt(double a, double b, double alpha, double g, double tol, int depth) {
+  double i8 = gl_voigt(0, a, b, alpha, g), i16 = gl_voigt(1, a, b, alpha, g);
+  if (fabs(i16 - i8) <= tol || depth >= 30) return i16;
+  double m = 0.5 * (a + b);
+  return adapt_voigt(a, m, alpha, g, tol, depth + 1) + adapt_voigt(m, b, alpha, g, tol, depth + 1);
+}
+
+static double integrate_voigt(double a, double b, double alpha, double g) {
+  double tol = 1e-13 * fabs(gl_voigt(1, a, b, alpha, g)) + 1e-300;
+  return adapt_voigt(a, b, alpha, g, tol, 0);
+}
+
+/* Average over the bin [x - dnu/2, x + dnu/2] of the base profile kind & 3. */
+static double prof_binned(int kind, double x, double dnu, double a, double g) {
+  double lo = x - 0.5 * dnu, hi = x + 0.5 * dnu;
+  int base = kind & 3;
+  if (base == ORC_LORENTZ) {
+    /* atan(tb) - atan(ta) = atan((tb - ta) / (1 + ta tb)) (+ pi when 1 + ta tb < 0) */
+    double ta = lo / g, tb = hi / g, p = 1.0 + ta * tb;
+    double d = atan((tb - ta) / p) + (p < 0.0 ? ORC_PI : 0.0);
+    return d / (ORC_PI * dnu);
+  }
+  if (base == ORC_VOIGT) {
+    if (!gl_ready) gl_init();
+    if (lo < 0.0 && hi > 0.0)   /* split at the line centre, where the profile peaks */
+      return (integrate_voigt(lo, 0.0, a, g) + integrate_voigt(0.0, hi, a, g)) / dnu;
+    return integrate_voigt(lo, hi, a, g) / dnu;
+  }
+  /* Gaussian: mass = (erf(tb) - erf(ta)) / 2, t = u sqrt(ln2) / alpha; erfc on one side */
+  double c = sqrt(ORC_LN2) / a, ta = lo * c, tb = hi * c, mass;
+  if (ta >= 0.0) mass = 0.5 * (erfc(ta) - erfc(tb));
+  else if (tb <= 0.0) mass = 0.5 * (erfc(-tb) - erfc(-ta));
+  else mass = 0.5 * (erf(tb) - erf(ta));
+  return mass / dnu;
+}
+
+/* Profile value at a grid point: sampled (kinds 0..3) or bin-averaged (kinds 4..7). */
+static double prof_point(int kind, double x, double dnu, double a, double g) {
+  if (kind & ORC_BINNED) return prof_binned(kind, x, dnu, a, g);
+  if (kind == ORC_LORENTZ) return prof_lorentz(x, g);
+  if (kind == ORC_VOIGT) return prof_voigt(x, a, g);
+  return prof_gauss(x, a);
+}
+
+void orc_profile_binned(int kind, int64_t n, const double* x, double dnu, double a, double g, double* f) {
+  if (!gl_ready) gl_init();
+  for (int64_t i = 0; i < n; ++i) f[i] = prof_binned(kind | ORC_BINNED, x[i], dnu, a, g);
 }
 
 /* ---------------------------------------------------------------------------
@@ -469,6 +567,7 @@ void orc_widths(int kind, const double* nu, const float* gamma_ref, const float*
                 double T, double P, double mass_da, double hwhm, double T_ref,
                 double* alpha, double* gamma) {
   double dop = sqrt(2.0 * ORC_NA * ORC_KB * T * ORC_LN2 / mass_da) / ORC_C;
+  kind &= 3;  /* binned kinds take the widths of their base kind */
   for (int64_t t = 0; t < n; ++t) {
     alpha[t] = kind == ORC_GAUSS_HWHM ? hwhm : nu[t] * dop;
     gamma[t] = (kind == ORC_LORENTZ || kind == ORC_VOIGT)
@@ -486,6 +585,7 @@ void orc_widths(int kind, const double* nu, const float* gamma_ref, const float*
 int orc_cross_section(int kind, const double* nu, const double* I, const double* alpha, const double* gamma,
                       const uint8_t* keep, const int64_t* ilo, const int64_t* ihi, int64_t n,
                       double nu_min, double dnu, int64_t n_grid, double* sigma) {
+  if (!gl_ready) gl_init();
   for (int64_t i = 0; i < n_grid; ++i) sigma[i] = 0.0;
   int64_t nblk = 256;
   int64_t bs = (n_grid + nblk - 1) / nblk;
@@ -499,11 +599,7 @@ int orc_cross_section(int kind, const double* nu, const double* I, const double*
       int64_t lo = ilo[t] > a0 ? ilo[t] : a0, hi = ihi[t] < a1 ? ihi[t] : a1;
       for (int64_t i = lo; i <= hi; ++i) {
         double x = (nu_min + (double)i * dnu) - nu[t];
-        double f;
-        if (kind == ORC_LORENTZ) f = prof_lorentz(x, gamma[t]);
-        else if (kind == ORC_VOIGT) f = prof_voigt(x, alpha[t], gamma[t]);
-        else f = prof_gauss(x, alpha[t]);
-        sigma[i] += I[t] * f;
+        sigma[i] += I[t] * prof_point(kind, x, dnu, alpha[t], gamma[t]);
       }
     }
   }
@@ -514,17 +610,14 @@ int orc_cross_section(int kind, const double* nu, const double* I, const double*
 int orc_cross_section_window(int kind, const double* nu, const double* I, const double* alpha, const double* gamma,
                              const uint8_t* keep, const int64_t* ilo, const int64_t* ihi, int64_t n,
                              double nu_min, double dnu, int64_t i0, int64_t m, double* sigma) {
+  if (!gl_ready) gl_init();
   for (int64_t j = 0; j < m; ++j) sigma[j] = 0.0;
   for (int64_t t = 0; t < n; ++t) {
     if (!keep[t] || ihi[t] < i0 || ilo[t] > i0 + m - 1) continue;
     int64_t lo = ilo[t] > i0 ? ilo[t] : i0, hi = ihi[t] < i0 + m - 1 ? ihi[t] : i0 + m - 1;
     for (int64_t i = lo; i <= hi; ++i) {
       double x = (nu_min + (double)i * dnu) - nu[t];
-      double f;
-      if (kind == ORC_LORENTZ) f = prof_lorentz(x, gamma[t]);
-      else if (kind == ORC_VOIGT) f = prof_voigt(x, alpha[t], gamma[t]);
-      else f = prof_gauss(x, alpha[t]);
-      sigma[i - i0] += I[t] * f;
+      sigma[i - i0] += I[t] * prof_point(kind, x, dnu, alpha[t], gamma[t]);
     }
   }
   return ORC_OK;
@@ -557,6 +650,7 @@ int orc_cross_section_grad(int kind, const double* E, const double* E_vib,
                            int64_t n, double T, double T_vib, double P, double T_ref, const double* Qd,
                            double nu_min, double dnu, const double* w,
                            double* dA, double* dgref, double* G, double* Gabs, double* scal) {
+  if (kind & ORC_BINNED) return ORC_ERR_ARG;  /* the adjoint covers the sampled profiles */
   const double c2 = orc_c2();
   double* cT = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
   double* cTv = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
