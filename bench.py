@@ -397,7 +397,9 @@ def main_pxc(args):
 
 
 def run_extras(args, pxc, torch, dev, synth):
-    """Batched (T, P) table vs sequential plain calls; forward+backward vs forward."""
+    """Batched (T, P) table vs sequential plain calls; forward+backward vs forward; non-LTE
+    population models and emission; binned profiles on a coarse grid; the cooling function."""
+    import numpy as np
     res = {}
     stream = torch.cuda.current_stream(dev)
 
@@ -478,6 +480,55 @@ def run_extras(args, pxc, torch, dev, synth):
     ms_fb = timed(fb, reps=3)
     res["fwd_bwd"] = {"workload": w.name, "lines": w.n_trans, "fwd_ms": ms_f, "fwd_bwd_ms": ms_fb,
                       "ratio": ms_fb / ms_f}
+
+    # vibronic-density populations on the same list (T_rot = 1200 K), absorption and emission
+    nv = torch.from_numpy(w.vib_densities()).to(dev)
+    std = pxc.States(st.E, st.g, st.E_vib, nv)
+    ms_d = timed(lambda: pxc.pxc_cross_section(wsf, std, tr, (w.T, 0.0, w.P), grid, prof), reps=3)
+    wsf.set_emission(True)
+    ms_de = timed(lambda: pxc.pxc_cross_section(wsf, std, tr, (w.T, 0.0, w.P), grid, prof), reps=3)
+    ms_2e = timed(lambda: pxc.pxc_cross_section(wsf, st, tr, cond, grid, prof), reps=3)
+    wsf.set_emission(False)
+    res["nlte_models"] = {"workload": w.name, "lines": w.n_trans, "treanor_abs_ms": ms_f,
+                          "density_abs_ms": ms_d, "density_em_ms": ms_de, "treanor_em_ms": ms_2e}
+    del wsf, st, std, tr, prof
+    torch.cuda.empty_cache()
+
+    # binned profiles on the 0.1 cm^-1 grid of doppler_1e5 (1e5 lines, widths far below the bin)
+    w = synth.workload("doppler_1e5")
+    E, g, _ = w.states()
+    up, lo, A = w.transitions()
+    gr, ne = w.broadening()
+    st = pxc.States(torch.from_numpy(E).to(dev), torch.from_numpy(g).to(dev), None)
+    tr = pxc.Transitions(torch.from_numpy(up).to(dev), torch.from_numpy(lo).to(dev), torch.from_numpy(A).to(dev))
+    grid = (w.nu_min, w.dnu, w.n_grid)
+    wsb = pxc.Workspace(max_states=w.n_states, max_lines=w.n_trans, max_grid=w.n_grid, device=dev)
+    binned = {}
+    for kind in ("gauss_doppler", "binned_gauss_doppler", "voigt", "binned_voigt"):
+        prof = pxc.Profile(kind, w.cutoff, w.mass_da, 0.0, torch.from_numpy(gr).to(dev), torch.from_numpy(ne).to(dev))
+        ms_k = timed(lambda: pxc.pxc_cross_section(wsb, st, tr, (w.T, 0.0, 1.0), grid, prof), reps=3)
+        ev = wsb.stats()["evals_nonzero"]
+        binned[kind] = {"ms": ms_k, "evals": ev, "evals_per_s": ev / (ms_k / 1e3)}
+    res["binned_profiles"] = {"workload": w.name, "lines": w.n_trans, "grid_step": w.dnu, **binned}
+    del wsb, st, tr
+    torch.cuda.empty_cache()
+
+    # cooling function on one 1e8-line chunk of voigt_1e9 (5e7 states), 20 temperatures
+    w = synth.workload("voigt_1e9")
+    n = min(w.chunk, 100_000_000)
+    E, g, _ = w.states()
+    st = pxc.States(torch.from_numpy(E).to(dev), torch.from_numpy(g).to(dev), None)
+    up = torch.empty(n, dtype=torch.int32); lo = torch.empty(n, dtype=torch.int32)
+    A = torch.empty(n, dtype=torch.float32)
+    w.transitions(0, n, out=(up.numpy(), lo.numpy(), A.numpy()))
+    tr = pxc.Transitions(up.to(dev), lo.to(dev), A.to(dev))
+    Ts = [float(t) for t in np.geomspace(100.0, 5000.0, 20)]
+    wsc = pxc.Workspace(max_states=w.n_states, max_lines=n, max_grid=1, max_conditions=len(Ts), device=dev)
+    ms_c = timed(lambda: pxc.pxc_cooling_function(wsc, st, tr, [(t, 0.0, 1.0) for t in Ts]), reps=3)
+    res["cooling_function"] = {"workload": w.name, "lines": n, "states": w.n_states, "temperatures": len(Ts),
+                               "ms": ms_c, "lines_per_s": n / (ms_c / 1e3)}
+    del wsc, st, tr
+    torch.cuda.empty_cache()
     return res
 
 

@@ -102,7 +102,16 @@ typedef enum {
   PXC_GAUSS_DOPPLER = 0, /* Doppler HWHM alpha = (nu/c) sqrt(2 N_A k_B T ln2 / M) */
   PXC_GAUSS_HWHM = 1,    /* Gaussian with the fixed HWHM `hwhm` */
   PXC_LORENTZ = 2,       /* gamma = gamma_ref (T_ref/T)^n_T P */
-  PXC_VOIGT = 3          /* Voigt of the Doppler alpha and the Lorentz gamma */
+  PXC_VOIGT = 3,         /* Voigt of the Doppler alpha and the Lorentz gamma */
+  /* Binned profiles (Table profile): the average of the profile over the grid bin
+   * [nu_i - dnu/2, nu_i + dnu/2] centred on each point, so sum_i sigma_i dnu keeps the line
+   * intensity on any grid (no undersampling loss).  Widths as the base kind (kind & 3).
+   * Forward only (pxc_cross_section_backward returns PXC_ERR_ARG). */
+  PXC_BINNED_GAUSS_DOPPLER = 4, /* erf / erfc differences */
+  PXC_BINNED_GAUSS_HWHM = 5,
+  PXC_BINNED_LORENTZ = 6,       /* arctangent difference */
+  PXC_BINNED_VOIGT = 7          /* composite 2-point Gauss-Legendre over the bin, subintervals of a
+                                   quarter of the local width scale, at most 1024 per bin */
 } pxc_profile;
 
 typedef struct {

@@ -20,7 +20,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpxc.so")
 
 PXC_GAUSS_DOPPLER, PXC_GAUSS_HWHM, PXC_LORENTZ, PXC_VOIGT = 0, 1, 2, 3
-PROFILES = {"gauss_doppler": 0, "gauss_hwhm": 1, "lorentz": 2, "voigt": 3}
+PROFILES = {"gauss_doppler": 0, "gauss_hwhm": 1, "lorentz": 2, "voigt": 3,
+            "binned_gauss_doppler": 4, "binned_gauss_hwhm": 5, "binned_lorentz": 6, "binned_voigt": 7}
 PXC_EXP_EMPTY = -2147483648
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_ID_RANGE", 3: "ERR_NONFINITE", 4: "ERR_OVERFLOW", 5: "ERR_TIMEOUT",
           6: "ERR_CUDA", 7: "ERR_CAPACITY"}
@@ -402,7 +403,7 @@ def pxc_cross_section_streamed(ws: Workspace, states: States, upper, lower, A, g
     """Host-resident (preferably pinned) transition arrays streamed in chunks of the workspace's max_lines."""
     arr, _ = _conds(cond)
     L = load()
-    broad = profile.kind in ("lorentz", "voigt")
+    broad = profile.kind in ("lorentz", "voigt", "binned_lorentz", "binned_voigt")
     a32 = int(A.dtype == torch.float32)
     nb = L.pxc_stream_buffer_bytes(ws.cap.max_lines, a32, int(broad))
     if bufs is None:

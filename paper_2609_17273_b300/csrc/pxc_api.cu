@@ -182,10 +182,10 @@ struct WsExtra {
   unsigned long long* h_cnt;
   cudaStream_t copy_stream;
   cudaEvent_t ev_copied[2], ev_done[2];
-  int occ[4][kNumTiles];  // resident profile CTAs per SM for each kind and tile
+  int occ[kNumKinds][kNumTiles];  // resident profile CTAs per SM for each kind and tile
   int emission;           // emission intensities instead of absorption
   const double* cache_nvib;  // densities the cached Boltzmann table was built with
-  int tile[4][2];         // tile used for each kind, [single condition, batched]
+  int tile[kNumKinds][2];         // tile used for each kind, [single condition, batched]
   // last call
   int64_t last_nseg;
   int last_seg, last_tile;
@@ -248,13 +248,14 @@ CondDev make_cond(const pxc_condition& c, const pxc_profile_args& pa, int slot) 
 
 pxc_status check_prof(const pxc_profile_args* pa, const pxc_transitions* tr) {
   if (!pa) return fail(PXC_ERR_ARG, "profile args: null");
-  if (pa->kind < PXC_GAUSS_DOPPLER || pa->kind > PXC_VOIGT) return fail(PXC_ERR_ARG, "profile: unknown kind");
-  if ((pa->kind == PXC_GAUSS_DOPPLER || pa->kind == PXC_VOIGT) && !(pa->mass_da > 0.0))
+  if (pa->kind < PXC_GAUSS_DOPPLER || pa->kind > PXC_BINNED_VOIGT) return fail(PXC_ERR_ARG, "profile: unknown kind");
+  const int base = pa->kind & 3;  // binned kinds take the widths of their base kind
+  if ((base == PXC_GAUSS_DOPPLER || base == PXC_VOIGT) && !(pa->mass_da > 0.0))
     return fail(PXC_ERR_ARG, "profile: mass must be > 0");
-  if (pa->kind == PXC_GAUSS_HWHM && !(pa->hwhm > 0.0)) return fail(PXC_ERR_ARG, "profile: hwhm must be > 0");
-  if ((pa->kind == PXC_LORENTZ || pa->kind == PXC_VOIGT) && tr->n > 0 && (bad_ptr(pa->gamma_ref) || bad_ptr(pa->n_T)))
+  if (base == PXC_GAUSS_HWHM && !(pa->hwhm > 0.0)) return fail(PXC_ERR_ARG, "profile: hwhm must be > 0");
+  if ((base == PXC_LORENTZ || base == PXC_VOIGT) && tr->n > 0 && (bad_ptr(pa->gamma_ref) || bad_ptr(pa->n_T)))
     return fail(PXC_ERR_ARG, "profile: gamma_ref and n_T required");
-  if ((pa->kind == PXC_LORENTZ || pa->kind == PXC_VOIGT) && !(pa->T_ref > 0.0))
+  if ((base == PXC_LORENTZ || base == PXC_VOIGT) && !(pa->T_ref > 0.0))
     return fail(PXC_ERR_ARG, "profile: T_ref must be > 0");
   if (!(pa->cutoff >= 0.0)) return fail(PXC_ERR_ARG, "profile: cutoff must be >= 0");
   return PXC_OK;
@@ -392,7 +393,7 @@ pxc_status pxc_workspace_create(const pxc_capacity* cap, void* scratch, size_t b
     cudaEventCreateWithFlags(&x->ev_copied[i], cudaEventDisableTiming);
     cudaEventCreateWithFlags(&x->ev_done[i], cudaEventDisableTiming);
   }
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < kNumKinds; ++k) {
     for (int t = 0; t < kNumTiles; ++t) x->occ[k][t] = profile_occupancy(k, t);
     // defaults: narrow segments balance dense single-condition spectra best; batched
     // tables (most lines zero in most conditions) pay less staging with wide segments
@@ -548,7 +549,7 @@ pxc_status pxc_cross_section(pxc_workspace* ws, const pxc_states* st, const pxc_
   if (!(threshold >= 0.0)) return fail(PXC_ERR_ARG, "threshold must be >= 0");
   for (int i = 0; i < n_c; ++i) {
     if ((r = check_cond(c[i], false, st))) return r;
-    if (pa->kind == PXC_LORENTZ && !(c[i].P > 0.0)) return fail(PXC_ERR_ARG, "Lorentzian profile needs P > 0");
+    if ((pa->kind & 3) == PXC_LORENTZ && !(c[i].P > 0.0)) return fail(PXC_ERR_ARG, "Lorentzian profile needs P > 0");
     if (!(c[i].P >= 0.0)) return fail(PXC_ERR_ARG, "condition: P must be >= 0");
   }
   WsExtra* x = X(ws);
@@ -674,6 +675,7 @@ pxc_status pxc_cross_section_backward(pxc_workspace* ws, const pxc_states* st, c
   if (ws->accumulate) return fail(PXC_ERR_ARG, "backward: accumulate mode is forward-only");
   if (x->emission || st->n_vib)
     return fail(PXC_ERR_ARG, "backward: absorption with LTE or two-temperature populations only");
+  if (pa->kind & 4) return fail(PXC_ERR_ARG, "backward: sampled profiles only (binned kinds are forward-only)");
   GridP gp = make_gridp(*grid, pa->cutoff);
   unsigned long long* cnt = at<unsigned long long>(ws, L.counters);
   cudaMemsetAsync(cnt, 0, CNT_N * 8, s);
@@ -738,14 +740,14 @@ pxc_status pxc_get_stats(pxc_workspace* ws, cudaStream_t s, pxc_stats* out) {
 }
 
 pxc_status pxc_set_tile(pxc_workspace* ws, int32_t kind, int32_t batched, int32_t tile) {
-  if (!ws || kind < 0 || kind > 3 || batched < 0 || batched > 1 || tile < 0 || tile >= kNumTiles)
+  if (!ws || kind < 0 || kind >= kNumKinds || batched < 0 || batched > 1 || tile < 0 || tile >= kNumTiles)
     return fail(PXC_ERR_ARG, "set_tile: bad arguments");
   X(ws)->tile[kind][batched] = tile;
   return PXC_OK;
 }
 
 pxc_status pxc_get_tile(pxc_workspace* ws, int32_t kind, int32_t batched, int32_t* tile) {
-  if (!ws || !tile || kind < 0 || kind > 3 || batched < 0 || batched > 1)
+  if (!ws || !tile || kind < 0 || kind >= kNumKinds || batched < 0 || batched > 1)
     return fail(PXC_ERR_ARG, "get_tile: bad arguments");
   *tile = X(ws)->tile[kind][batched];
   return PXC_OK;
@@ -755,7 +757,7 @@ pxc_status pxc_autotune(pxc_workspace* ws, const pxc_states* st, const pxc_trans
                         int32_t n_c, const pxc_grid* grid, const pxc_profile_args* pa, double threshold,
                         float* sigma_out, int32_t* sigma_exp_out, int32_t repeats, int32_t* tile_out,
                         double* ms_out, cudaStream_t s) {
-  if (!ws || !pa || pa->kind < 0 || pa->kind > 3 || n_c < 1 || repeats < 1)
+  if (!ws || !pa || pa->kind < 0 || pa->kind >= kNumKinds || n_c < 1 || repeats < 1)
     return fail(PXC_ERR_ARG, "autotune: bad arguments");
   if (ws->accumulate) return fail(PXC_ERR_ARG, "autotune: not in accumulate mode (runs the call repeatedly)");
   WsExtra* x = X(ws);

@@ -104,7 +104,7 @@ def test_autotune_picks_a_tile_and_keeps_result(pxc, poly, poly_ref):
 
 def test_tile_arguments_checked(pxc, poly):
     ws = _ws(pxc, poly)
-    for args in [(4, False, 0), (-1, False, 0), (0, False, pxc.NUM_TILES), (0, False, -1)]:
+    for args in [(8, False, 0), (-1, False, 0), (0, False, pxc.NUM_TILES), (0, False, -1)]:
         with pytest.raises(pxc.PxcError) as ei:
             ws.set_tile(*args)
         assert ei.value.code == 1
