@@ -4,6 +4,13 @@
 
 namespace pxc {
 
+// Slots of the workspace's u64 counter block: work-queue head, items, kept lines, lines with
+// non-zero scaled intensity, window evaluations (all / non-zero lines), line-segment pairs, raw
+// item total; CNT_N slots in all.
+enum { CNT_QUEUE = 0, CNT_ITEMS = 1, CNT_KEPT = 2, CNT_NONZERO = 3, CNT_EVALS = 4, CNT_EVALS_NZ = 5, CNT_ALL = 6,
+       CNT_ITEMS_RAW = 7, CNT_N = 16 };
+
+
 // Kernel launches issued by the library since load (all workspaces, all threads).
 void note_launches(int n);
 int64_t launches_total();

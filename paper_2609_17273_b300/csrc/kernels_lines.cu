@@ -12,7 +12,6 @@ static std::atomic<int64_t> g_launches{0};
 void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 int64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
-enum { CNT_QUEUE = 0, CNT_ITEMS = 1, CNT_KEPT = 2, CNT_NONZERO = 3, CNT_EVALS = 4, CNT_EVALS_NZ = 5 };
 
 __device__ __forceinline__ void set_err(unsigned* err, unsigned bits) { atomicOr(err, bits); }
 
@@ -1025,92 +1024,97 @@ void launch_segments(const int4* pos, const unsigned long long* n_dev, int64_t n
 }
 
 // Work items: each (condition, segment) group is split into ceil(lines / item_lines) items (at least one).
-__global__ void k_items(const int32_t* __restrict__ segr, int64_t nseg, int n_c, int item_lines_max,
-                        int32_t* __restrict__ seg_items, Item* __restrict__ items,
-                        unsigned long long* __restrict__ counters, int64_t max_items, int64_t target_items,
-                        int64_t max_partial) {
-  __shared__ unsigned long long part[1024];
-  __shared__ int item_lines_sh;
-  const int64_t ng = nseg * n_c;
-  int64_t per = (ng + blockDim.x - 1) / blockDim.x;
-  int64_t a = threadIdx.x * per, b = a + per < ng ? a + per : ng;
-  // Lines per item: about target_items equal items over all segments (load balance of the
-  // persistent profile kernel), at least 1024, never more split items than partial rows.
-  {
-    unsigned long long tot = 0;
-    for (int64_t i = a; i < b; ++i) {
-      int64_t s = i % nseg;
-      tot += (unsigned long long)(segr[nseg + s] - segr[s]);
-    }
-    part[threadIdx.x] = tot;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      unsigned long long all = 0;
-      for (int i = 0; i < (int)blockDim.x; ++i) all += part[i];
-      long long L = item_lines_max;
-      if (target_items > 0) {  // only the single-condition call splits (its partial rows are reduced)
-        long long t = (long long)((all + target_items - 1) / target_items);
-        long long m = (long long)((all + max_partial - 1) / (max_partial > 0 ? max_partial : 1));
-        t = t > 512 ? t : 512;
-        t = t > m ? t : m;
-        t = (t + 255) / 256 * 256;
-        L = t < item_lines_max ? t : item_lines_max;
-      }
-      item_lines_sh = (int)L;
-    }
-    __syncthreads();
+// Work items of the profile kernel, in four launches over all (condition, segment) pairs:
+// total line-segment pairs (integer atomics), items per pair, exclusive scan, emission.
+// Lines per item: about target_items equal items over all segments (load balance of the
+// persistent profile kernel), at least 512, never more split items than partial rows; only
+// the single-condition call splits (its partial rows are reduced), batched calls use
+// item_lines_max.
+__device__ __forceinline__ int item_lines_of(unsigned long long all, int item_lines_max, int64_t target_items,
+                                             int64_t max_partial) {
+  long long L = item_lines_max;
+  if (target_items > 0) {
+    long long t = (long long)((all + target_items - 1) / target_items);
+    long long m = (long long)((all + max_partial - 1) / (max_partial > 0 ? max_partial : 1));
+    t = t > 512 ? t : 512;
+    t = t > m ? t : m;
+    t = (t + 255) / 256 * 256;
+    L = t < item_lines_max ? t : item_lines_max;
   }
-  const int item_lines = item_lines_sh;
-  auto count = [&](int64_t gi) -> int64_t {
-    int64_t s = gi % nseg;
-    int64_t nl = (int64_t)segr[nseg + s] - segr[s];
-    int64_t c = (nl + item_lines - 1) / item_lines;
-    return c < 1 ? 1 : c;
-  };
-  unsigned long long sum = 0;
-  for (int64_t i = a; i < b; ++i) sum += count(i);
-  part[threadIdx.x] = sum;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long run = 0;
-    for (int i = 0; i < (int)blockDim.x; ++i) { unsigned long long v = part[i]; part[i] = run; run += v; }
-    seg_items[ng] = (int32_t)run;
+  return (int)L;
+}
+
+__global__ void __launch_bounds__(256) k_items_total(const int32_t* __restrict__ segr, int64_t nseg,
+                                                     unsigned long long* __restrict__ counters) {
+  unsigned long long tot = 0;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += (int64_t)gridDim.x * blockDim.x)
+    tot += (unsigned long long)(segr[nseg + s] - segr[s]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, o);
+  if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&counters[CNT_ALL], tot);
+}
+
+__global__ void __launch_bounds__(256) k_items_count(const int32_t* __restrict__ segr, int64_t nseg, int n_c,
+                                                     int item_lines_max, const unsigned long long* __restrict__ counters,
+                                                     int64_t target_items, int64_t max_partial,
+                                                     uint32_t* __restrict__ cnt) {
+  const int L = item_lines_of(counters[CNT_ALL] * (unsigned long long)n_c, item_lines_max, target_items, max_partial);
+  const int64_t ng = nseg * n_c;
+  for (int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gi < ng; gi += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = gi % nseg;
+    const int64_t nl = (int64_t)segr[nseg + s] - segr[s];
+    const int64_t c = (nl + L - 1) / L;
+    cnt[gi] = (uint32_t)(c < 1 ? 1 : c);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_items_emit(const int32_t* __restrict__ segr, int64_t nseg, int n_c,
+                                                    int item_lines_max, const int32_t* __restrict__ seg_items,
+                                                    Item* __restrict__ items, unsigned long long* __restrict__ counters,
+                                                    int64_t max_items, int64_t target_items, int64_t max_partial) {
+  const int L = item_lines_of(counters[CNT_ALL] * (unsigned long long)n_c, item_lines_max, target_items, max_partial);
+  const int64_t ng = nseg * n_c;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const unsigned long long run = (unsigned long long)(uint32_t)seg_items[ng];
     counters[CNT_ITEMS] = run < (unsigned long long)max_items ? run : (unsigned long long)max_items;
     counters[CNT_QUEUE] = 0;
   }
-  __syncthreads();
-  unsigned long long run = part[threadIdx.x];
-  for (int64_t gi = a; gi < b; ++gi) {
-    int64_t c = count(gi);
-    seg_items[gi] = (int32_t)run;
-    int64_t s = gi % nseg;
-    int32_t f = segr[s], e = segr[nseg + s];
-    for (int64_t k = 0; k < c; ++k) {
+  for (int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gi < ng; gi += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t first = seg_items[gi], c = seg_items[gi + 1] - first;
+    const int64_t s = gi % nseg;
+    const int32_t f = segr[s], e = segr[nseg + s];
+    for (int32_t k = 0; k < c; ++k) {
+      const int64_t idx = (int64_t)first + k;
+      if (idx >= max_items) break;  // sized on the host; never taken for calls that passed the capacity check
       Item it;
       it.cond = (int32_t)(gi / nseg);
       it.seg = (int32_t)s;
-      it.begin = (int32_t)(f + k * item_lines);
-      int64_t en = (int64_t)f + (k + 1) * item_lines;
+      it.begin = (int32_t)(f + (int64_t)k * L);
+      const int64_t en = (int64_t)f + (int64_t)(k + 1) * L;
       it.end = (int32_t)(en < e ? en : e);
       if (it.begin > e) it.begin = e;
-      int64_t idx = (int64_t)run + k;
-      if (idx >= max_items) break;  // sized on the host; never taken for calls that passed the capacity check
       it.slot = k == 0 ? -1 : (int32_t)(idx - gi - 1);
-      it.first_of_seg = (int32_t)run;
-      it.n_of_seg = (int32_t)c;
+      it.first_of_seg = first;
+      it.n_of_seg = c;
       it.pad = 0;
       items[idx] = it;
     }
-    run += c;
   }
 }
 
 void launch_items(const int32_t* segr, int64_t nseg, int n_c, int item_lines, int32_t* seg_items, Item* items,
                   unsigned long long* counters, int64_t max_items, int64_t target_items, int64_t max_partial,
                   cudaStream_t s) {
-  k_items<<<1, 1024, 0, s>>>(segr, nseg, n_c, item_lines, seg_items, items, counters, max_items, target_items,
-                             max_partial);
-  note_launches(1);
+  const int64_t ng = nseg * n_c;
+  cudaMemsetAsync(counters + CNT_ALL, 0, sizeof(unsigned long long), s);
+  auto blocks = [](int64_t n) { int64_t b = (n + 255) / 256; return (unsigned)(b < 1 ? 1 : (b > 148 * 8 ? 148 * 8 : b)); };
+  k_items_total<<<blocks(nseg), 256, 0, s>>>(segr, nseg, counters);
+  k_items_count<<<blocks(ng), 256, 0, s>>>(segr, nseg, n_c, item_lines, counters, target_items, max_partial,
+                                           reinterpret_cast<uint32_t*>(seg_items));
+  k_scan_counts<<<1, 1024, 0, s>>>(reinterpret_cast<uint32_t*>(seg_items), ng, counters + CNT_ITEMS_RAW);
+  k_items_emit<<<blocks(ng), 256, 0, s>>>(segr, nseg, n_c, item_lines, seg_items, items, counters, max_items,
+                                          target_items, max_partial);
+  note_launches(4);
 }
 
 // Adds the partial rows of split segments to sigma, in item order (deterministic).

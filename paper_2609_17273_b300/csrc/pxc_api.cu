@@ -30,7 +30,6 @@ pxc_status cuda_check(const char* where) {
   return PXC_OK;
 }
 
-enum { CNT_QUEUE = 0, CNT_ITEMS = 1, CNT_KEPT = 2, CNT_NONZERO = 3, CNT_EVALS = 4, CNT_EVALS_NZ = 5, CNT_N = 16 };
 
 constexpr int kWinCap = 16384;  // largest cut-off window (points) the item tables are sized for
 
