@@ -44,7 +44,7 @@ __device__ __forceinline__ T warp_sum(T v) {
 // ------------------------------------------------------------------ K-Q: Boltzmann table and Q
 // b_s = exp(-c2 E_s / T) (LTE, Eq. pf), exp(-c2 E_vib/T_vib - c2 E_rot/T_rot) (Eq. Q nlte 2T) or
 // n_vib exp(-c2 E_rot / T_rot) (vibronic densities, Eq. Q nlte Nvib); per-block partial sums of
-// g b, g b c2 E_rot / T, g b c2 E_vib / T_vib and (cooling function) g b S in a fixed order.
+// g b, g b E_rot, g b E_vib and (cooling function) g b S in a fixed order.
 __global__ void __launch_bounds__(kThreadsQ) k_boltzmann(const double* __restrict__ E, const int32_t* __restrict__ g,
                                                          const double* __restrict__ Ev,
                                                          const double* __restrict__ nvib, int64_t n,
@@ -92,9 +92,9 @@ __global__ void __launch_bounds__(kThreadsQ) k_boltzmann(const double* __restric
           if (dens) lb += log2(w);
           double term = (double)g[s] * b;
           q0 += term;
-          q1 += term * er * sp.c2_T;   // divided by T in k_qfinal: dQ/dT = sum g b c2 E_rot / T^2
-          q2 += term * ev * sp.c2_Tv;  // divided by T_vib: dQ/dT_vib (0 unless two temperatures)
-          if (Ssum) q3 += term * Ssum[s];
+          q1 = fma(term, er, q1);                // times c2 / T^2 in k_qfinal: dQ/dT (or dQ/dT_rot)
+          if (two_t) q2 = fma(term, ev, q2);     // times c2 / T_vib^2: dQ/dT_vib
+          if (Ssum) q3 = fma(term, Ssum[s], q3);
         }
       }
       if (srec) srec[(int64_t)sl * stride + s] = make_double2(e, b);
@@ -145,8 +145,8 @@ __global__ void k_qfinal(const double* __restrict__ qpart, int nblk, int nslot, 
     const SlotP sp = slots[sl];
     double* r = qres + sl * 4;
     r[0] = t[0];
-    r[1] = t[1] / sp.T;                                 // dQ/dT (or dQ/dT_rot)
-    r[2] = sp.c2_Tv > 0.0 ? t[2] / sp.T_vib : 0.0;      // dQ/dT_vib
+    r[1] = t[1] * sp.c2_T / sp.T;                                 // dQ/dT (or dQ/dT_rot)
+    r[2] = sp.c2_Tv > 0.0 ? t[2] * sp.c2_Tv / sp.T_vib : 0.0;      // dQ/dT_vib
     r[3] = 1.0 / (8.0 * kPi * kC * t[0]);
     if (W_out) W_out[sl] = kH * kC * t[3] / (4.0 * kPi * t[0]);
   }
@@ -721,22 +721,26 @@ void launch_compact(const uint64_t* key, int64_t n, const uint32_t* boff, uint64
 
 // ------------------------------------------------------------------ LSD radix sort, 8 passes of 8 bits
 // Pass: per-tile digit histogram -> per-digit exclusive scan over tiles -> stable scatter.
+// Per-tile digit histograms.  The grid is sized for the largest list; the CTAs stride over the
+// tiles the kept count actually fills (n is only known on the device).
 __global__ void __launch_bounds__(kSortThreads) k_hist(const uint64_t* __restrict__ key,
                                                        const unsigned long long* __restrict__ n_dev, int64_t nblk,
                                                        int shift, uint32_t* __restrict__ cnt) {
   __shared__ uint32_t h[256];
   const int64_t n = (int64_t)*n_dev;
-  const int64_t base = (int64_t)blockIdx.x * kSortTile;
-  h[threadIdx.x] = 0;
-  __syncthreads();
-  if (base < n) {
+  const int64_t act = (n + kSortTile - 1) / kSortTile;
+  for (int64_t t = blockIdx.x; t < act; t += gridDim.x) {
+    const int64_t base = t * kSortTile;
+    h[threadIdx.x] = 0;
+    __syncthreads();
     for (int i = 0; i < kSortItems; ++i) {
       int64_t j = base + i * kSortThreads + threadIdx.x;
       if (j < n) atomicAdd(&h[(unsigned)(key[j] >> shift) & 255u], 1u);
     }
+    __syncthreads();
+    cnt[(int64_t)threadIdx.x * nblk + t] = h[threadIdx.x];
+    __syncthreads();
   }
-  __syncthreads();
-  cnt[(int64_t)threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
 }
 
 // One CTA per digit: exclusive scan of that digit's row over the active tiles; row total at the end.
@@ -773,53 +777,54 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(const uint64_t* __rest
   __shared__ uint32_t wc[kSortThreads / 32][256];
   __shared__ uint32_t dbase[256];
   const int64_t n = (int64_t)*n_dev;
-  const int64_t base = (int64_t)blockIdx.x * kSortTile;
-  if (base >= n) return;
+  const int64_t act = (n + kSortTile - 1) / kSortTile;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int d = threadIdx.x; d < 256 * (kSortThreads / 32); d += kSortThreads) (&wc[0][0])[d] = 0;
-  // digit bases: exclusive scan of the row totals (thread d computes its own base serially over 256 -> cheap)
-  {
-    uint32_t s = 0;
-    for (int d = 0; d < (int)threadIdx.x; ++d) s += rowtot[d];
-    dbase[threadIdx.x] = s + cnt[(int64_t)threadIdx.x * nblk + blockIdx.x];
-  }
-  __syncthreads();
-  uint64_t kv[kSortItems];
-  uint32_t iv[kSortItems];
-  uint32_t rk[kSortItems];
   const unsigned lt = (1u << lane) - 1u;
+  // digit bases: exclusive scan of the row totals (thread d sums serially over 256 -> cheap)
+  uint32_t rbase = 0;
+  for (int d = 0; d < (int)threadIdx.x; ++d) rbase += rowtot[d];
+  for (int64_t t = blockIdx.x; t < act; t += gridDim.x) {
+    const int64_t base = t * kSortTile;
+    for (int d = threadIdx.x; d < 256 * (kSortThreads / 32); d += kSortThreads) (&wc[0][0])[d] = 0;
+    dbase[threadIdx.x] = rbase + cnt[(int64_t)threadIdx.x * nblk + t];
+    __syncthreads();
+    uint64_t kv[kSortItems];
+    uint32_t iv[kSortItems];
+    uint32_t rk[kSortItems];
 #pragma unroll
-  for (int i = 0; i < kSortItems; ++i) {
-    int64_t j = base + (int64_t)w * (32 * kSortItems) + i * 32 + lane;
-    bool v = j < n;
-    kv[i] = v ? key[j] : 0;
-    iv[i] = v ? idx[j] : 0;
-    unsigned d = v ? ((unsigned)(kv[i] >> shift) & 255u) : 256u;
-    unsigned peers = __match_any_sync(0xffffffffu, d);
-    unsigned b = d < 256u ? wc[w][d] : 0u;
-    __syncwarp();
-    if (d < 256u && lane == __ffs(peers) - 1) wc[w][d] = b + __popc(peers);
-    __syncwarp();
-    rk[i] = v ? (b + __popc(peers & lt)) | (d << 20) : 0xffffffffu;
-  }
-  __syncthreads();
-  // exclusive scan over warps for each digit
-  {
-    uint32_t run = 0;
-    for (int ww = 0; ww < kSortThreads / 32; ++ww) {
-      uint32_t t = wc[ww][threadIdx.x];
-      wc[ww][threadIdx.x] = run;
-      run += t;
+    for (int i = 0; i < kSortItems; ++i) {
+      int64_t j = base + (int64_t)w * (32 * kSortItems) + i * 32 + lane;
+      bool v = j < n;
+      kv[i] = v ? key[j] : 0;
+      iv[i] = v ? idx[j] : 0;
+      unsigned d = v ? ((unsigned)(kv[i] >> shift) & 255u) : 256u;
+      unsigned peers = __match_any_sync(0xffffffffu, d);
+      unsigned b = d < 256u ? wc[w][d] : 0u;
+      __syncwarp();
+      if (d < 256u && lane == __ffs(peers) - 1) wc[w][d] = b + __popc(peers);
+      __syncwarp();
+      rk[i] = v ? (b + __popc(peers & lt)) | (d << 20) : 0xffffffffu;
     }
-  }
-  __syncthreads();
+    __syncthreads();
+    // exclusive scan over warps for each digit
+    {
+      uint32_t run = 0;
+      for (int ww = 0; ww < kSortThreads / 32; ++ww) {
+        uint32_t x = wc[ww][threadIdx.x];
+        wc[ww][threadIdx.x] = run;
+        run += x;
+      }
+    }
+    __syncthreads();
 #pragma unroll
-  for (int i = 0; i < kSortItems; ++i) {
-    if (rk[i] == 0xffffffffu) continue;
-    unsigned d = rk[i] >> 20, r = rk[i] & 0xfffffu;
-    uint32_t p = dbase[d] + wc[w][d] + r;
-    okey[p] = kv[i];
-    oidx[p] = iv[i];
+    for (int i = 0; i < kSortItems; ++i) {
+      if (rk[i] == 0xffffffffu) continue;
+      unsigned d = rk[i] >> 20, r = rk[i] & 0xfffffu;
+      uint32_t p = dbase[d] + wc[w][d] + r;
+      okey[p] = kv[i];
+      oidx[p] = iv[i];
+    }
+    __syncthreads();  // wc and dbase are rebuilt for the next tile
   }
 }
 
@@ -828,12 +833,14 @@ void launch_radix_sort(uint64_t* key[2], uint32_t* idx[2], const unsigned long l
   int64_t nblk = (n_max + kSortTile - 1) / kSortTile;
   if (nblk == 0) return;
   uint32_t* rowtot = rcount + 256 * nblk;
+  // enough CTAs for about four per SM; they stride over the tiles the kept lines fill
+  const unsigned grid = (unsigned)(nblk < 148 * 4 ? nblk : 148 * 4);
   for (int pass = 0; pass < 8; ++pass) {
     int src = pass & 1, dst = src ^ 1;
     int shift = pass * 8;
-    k_hist<<<(unsigned)nblk, kSortThreads, 0, s>>>(key[src], n_dev, nblk, shift, rcount);
+    k_hist<<<grid, kSortThreads, 0, s>>>(key[src], n_dev, nblk, shift, rcount);
     k_rowscan<<<256, 1024, 0, s>>>(rcount, n_dev, nblk, rowtot);
-    k_scatter<<<(unsigned)nblk, kSortThreads, 0, s>>>(key[src], idx[src], n_dev, nblk, shift, rcount, rowtot,
+    k_scatter<<<grid, kSortThreads, 0, s>>>(key[src], idx[src], n_dev, nblk, shift, rcount, rowtot,
                                                       key[dst], idx[dst]);
   }
   note_launches(24);
