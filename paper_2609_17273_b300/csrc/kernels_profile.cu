@@ -353,7 +353,8 @@ __device__ __forceinline__ void line_constants(const int4 p4, const float2 pr, c
 
 // Class of a line for the warp owning points [a, a + WPTS) of the segment:
 // 0 nothing, 1 fast (inside the window, region I), 2 window edge (region I, lane mask),
-// 3 near the line core.
+// 3 near the line core (some point in W4 regions III/IV), 4 near the core but every point in
+// regions I/II (Voigt only).
 template <int KIND, int WPTS>
 __device__ __forceinline__ int line_class(const LineC& c, int a) {
   const int b = a + WPTS - 1;
@@ -364,7 +365,12 @@ __device__ __forceinline__ int line_class(const LineC& c, int a) {
     const float dmin = fmaxf(0.f, fmaxf(c.cen - (float)b, (float)a - c.cen));
     far = dmin > c.reach;
   }
-  if (!far) return 3;
+  if (!far) {
+    // near the centre: 4 if every point still has |x| + y >= 5.5 (W4 region II or I), else 3
+    const float dmin = fmaxf(0.f, fmaxf(c.cen - (float)b, (float)a - c.cen));
+    const float reach5 = fmaxf(5.5f - c.y, 0.f) * frcp(c.step) * 1.0001f;
+    return dmin > reach5 ? 4 : 3;
+  }
   return (c.lo <= a && c.hi >= b) ? 1 : 2;
 }
 
@@ -502,16 +508,60 @@ __device__ __forceinline__ void eval_fastmask(const LineC& c, int wbase, int lan
   }
 }
 
+// Region II real rational Re w = y N(X) / D(X), X = x^2, coefficients from Y = y^2 (see
+// eval_slow for the factored forms).
+struct RegionII {
+  float n0, n1, n2, n3, d0, d1, d2, d3;
+};
+__device__ __forceinline__ RegionII region2(float y) {
+  const float bq = 0.5641896f;
+  const float Y = y * y;
+  RegionII r;
+  r.n3 = bq;
+  r.n2 = bq * (3.f * Y - 4.5f);
+  r.n1 = bq * ((3.f * Y + 1.f) * Y + 5.25f);
+  r.n0 = 0.125f * bq * (2.f * Y + 5.f) * ((4.f * Y + 12.f) * Y + 3.f);
+  r.d3 = 4.f * Y - 6.f;
+  r.d2 = (6.f * Y - 6.f) * Y + 10.5f;
+  r.d1 = ((4.f * Y + 6.f) * Y + 9.f) * Y - 4.5f;
+  r.d0 = (((Y + 6.f) * Y + 10.5f) * Y + 4.5f) * Y + 0.5625f;
+  return r;
+}
+
+// Warps near the centre whose points all have |x| + y >= 5.5: the region II rational at every
+// point (W4's two-level continued fraction, at least as accurate as region I wherever that one
+// applies), window edges masked, no per-point branches.
+template <int KIND, int PTS>
+__device__ __forceinline__ void eval_mid(const LineC& c, int wbase, int lane, float* acc) {
+  if (KIND != PXC_VOIGT) return;
+  const unsigned span = (unsigned)(c.hi - c.lo);
+  const int rel0 = wbase + lane - c.lo;
+  const RegionII r = region2(c.y);
+  const float Ky = c.Kc * c.y;
+  const float x0 = fmaf((float)(wbase + lane) - c.pf, c.step, c.nfs);
+  const float s32 = 32.f * c.step;
+#pragma unroll
+  for (int k = 0; k < PTS; ++k) {
+    const float x = fmaf((float)k, s32, x0);
+    const float X = x * x;
+    const float N = fmaf(fmaf(fmaf(r.n3, X, r.n2), X, r.n1), X, r.n0);
+    const float D = fmaf(fmaf(fmaf(X + r.d3, X, r.d2), X, r.d1), X, r.d0);
+    acc[k] += (unsigned)(rel0 + 32 * k) <= span ? Ky * N * frcp(D) : 0.f;
+  }
+}
+
+// Warps near the line core (Voigt), some point in W4 regions III/IV: blocks of 32 points far
+// from the centre keep the region-I formula; elsewhere each point takes its W4 region.  Region
+// II (5.5 <= |x|+y < 15) is the real rational Re w = y N(X) / D(X) in X = x^2 (N cubic, D monic
+// quartic, coefficients from Y = y^2 once per line and warp; Humlicek's constants satisfy
+// a = 2.5 b, which gives the factored forms of region2); only |x|+y < 5.5 needs the complex
+// regions III/IV.  (Gathering the region III/IV points of a warp to evaluate them on full warps
+// measured slower than this divergent form.)
 template <int KIND, int PTS>
 __device__ __forceinline__ void eval_slow(const LineC& c, int wbase, int lane, const float* lk, float* acc) {
   if (KIND >= PXC_BINNED_GAUSS_DOPPLER) return;  // binned lines are never in the core class
   const unsigned span = (unsigned)(c.hi - c.lo);
-  const float bq = 0.5641896f;
-  const float Y = c.y * c.y;
-  const float n3 = bq, n2 = bq * (3.f * Y - 4.5f), n1 = bq * ((3.f * Y + 1.f) * Y + 5.25f);
-  const float n0 = 0.125f * bq * (2.f * Y + 5.f) * ((4.f * Y + 12.f) * Y + 3.f);
-  const float d3 = 4.f * Y - 6.f, d2 = (6.f * Y - 6.f) * Y + 10.5f, d1 = ((4.f * Y + 6.f) * Y + 9.f) * Y - 4.5f;
-  const float d0 = (((Y + 6.f) * Y + 10.5f) * Y + 4.5f) * Y + 0.5625f;
+  const RegionII r = region2(c.y);
   const float Ky = c.Kc * c.y;
 #pragma unroll
   for (int k = 0; k < PTS; ++k) {
@@ -535,8 +585,8 @@ __device__ __forceinline__ void eval_slow(const LineC& c, int wbase, int lane, c
     if (fabsf(x) + c.y >= 15.f) {
       v = fmaf(x2, c.K, c.KA) * frcp(fmaf(x2, x2 + c.B1, c.d));
     } else if (fabsf(x) + c.y >= 5.5f) {
-      const float N = fmaf(fmaf(fmaf(n3, x2, n2), x2, n1), x2, n0);
-      const float D = fmaf(fmaf(fmaf(x2 + d3, x2, d2), x2, d1), x2, d0);
+      const float N = fmaf(fmaf(fmaf(r.n3, x2, r.n2), x2, r.n1), x2, r.n0);
+      const float D = fmaf(fmaf(fmaf(x2 + r.d3, x2, r.d2), x2, r.d1), x2, r.d0);
       v = Ky * N * frcp(D);
     } else {
       v = c.Kc * w4_core_re(x, c.y);
@@ -671,6 +721,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_profile(const ProfP p) {
       for (int q = SL - 1; q >= SL - no; --q) {
         const LineC& c = my[q];
         if (c.masks == 2) eval_fastmask<KIND, PTS>(c, wbase, lane, acc);
+        else if (c.masks == 4) eval_mid<KIND, PTS>(c, wbase, lane, acc);
         else eval_slow<KIND, PTS>(c, wbase, lane, lk, acc);
       }
 #pragma unroll
