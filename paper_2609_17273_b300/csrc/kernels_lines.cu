@@ -63,9 +63,12 @@ __global__ void __launch_bounds__(kThreadsQ) k_boltzmann(const double* __restric
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
       double e = E[s];
       double b = 0.0, lb = -INFINITY;
-      if (isnan(e)) {
-        b = 0.0;
-      } else if (isinf(e)) {
+      // NaN / infinity from the exponent bits (integer tests, off the FP64 pipe)
+      const unsigned long long eb = (unsigned long long)__double_as_longlong(e);
+      const bool nonfinite = (eb & 0x7ff0000000000000ull) == 0x7ff0000000000000ull;
+      if (nonfinite && (eb & 0x000fffffffffffffull)) {
+        b = 0.0;  // NaN: an absent state (R15)
+      } else if (nonfinite) {
         bad |= ERRB_NONFINITE;
       } else {
         double x, er = e, ev = 0.0, w = 1.0;
