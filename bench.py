@@ -108,6 +108,22 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def slowest_rank_ms(ms_local: float, world: int, device=None) -> float:
+    """The job time of `world` independent replicas: the largest of the ranks' own times (one
+    MAX all-reduce of a scalar over the default process group; no data-path collective)."""
+    import torch
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(units_per_rank: float, steps: int, world: int, ms_max: float) -> float:
+    """Whole-job throughput: every rank processed units_per_rank per step for `steps` steps."""
+    return world * units_per_rank * steps / (ms_max / 1e3)
+
+
 # ----------------------------------------------------------------------------- reference arm (oracle)
 
 def oracle_sample_rate(w, E, g, n_lines, threads):
@@ -284,12 +300,9 @@ def main_pxc(args):
     tm = ws.timing()
     ws.set_timing(False)
     ws.sync()
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = world * evals * args.steps / (ms_max / 1e3)
-    lines_per_s = world * w.n_trans * args.steps / (ms_max / 1e3)
+    ms_max = slowest_rank_ms(ms, world, dev)
+    value = replica_rate(evals, args.steps, world, ms_max)
+    lines_per_s = replica_rate(w.n_trans, args.steps, world, ms_max)
 
     # ---------------------------------------------------------------- e2e through the host-streaming ABI call
     e2e = None
@@ -317,14 +330,11 @@ def main_pxc(args):
         e1.record(stream)
         barrier()
         ms_e = e0.elapsed_time(e1)
-        mt = torch.tensor([ms_e], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(mt, op=dist.ReduceOp.MAX)
-        ms_e = float(mt.item())
+        ms_e = slowest_rank_ms(ms_e, world, dev)
         h2d = w.n_trans * (4 + 4 + (4 if w.A_f32 else 8) + 8)
-        e2e = {"value": world * evals * n_e2e / (ms_e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e = {"value": replica_rate(evals, n_e2e, world, ms_e), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": w.n_grid * 4 + 4, "steps": n_e2e, "ms_per_step": ms_e / n_e2e,
-               "lines_per_s": world * w.n_trans * n_e2e / (ms_e / 1e3)}
+               "lines_per_s": replica_rate(w.n_trans, n_e2e, world, ms_e)}
 
     # ---------------------------------------------------------------- rooflines
     peaks, peak_src = _peaks()
