@@ -174,6 +174,13 @@ pxc_status pxc_set_accumulate(pxc_workspace* ws, int on);
  * exponent handling.  pxc_cross_section_backward is absorption-only (PXC_ERR_ARG here). */
 pxc_status pxc_set_emission(pxc_workspace* ws, int on);
 
+/* Bound, in SM clock cycles, of the profile kernel's waits for line records staged by bulk
+ * copies (default 4e9, about 2 s).  A wait that runs out sets PXC_ERR_TIMEOUT (returned by
+ * pxc_sync_status); its CTA lets the copies it issued land and returns, so the context and the
+ * workspace stay usable.  A limit of 0 makes the waits give up at once: the failure path can be
+ * exercised without any fault.  No counterpart in the paper.  PXC_ERR_ARG if cycles < 0. */
+pxc_status pxc_set_wait_limit(pxc_workspace* ws, int64_t cycles);
+
 /* Partition functions, Eq. (pf) (LTE) or Eq. (Q nlte 2T) (T_vib > 0), summed in
  * FP64 over all states for each of the n_c conditions.
  * Q_out:  [n_c] device.

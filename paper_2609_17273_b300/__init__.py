@@ -75,7 +75,7 @@ ABI_FUNCTIONS = [
     "pxc_cross_section_backward", "pxc_get_stats", "pxc_get_binning", "pxc_stream_buffer_bytes",
     "pxc_cross_section_streamed", "pxc_kernel_launches", "pxc_set_timing", "pxc_get_timing",
     "pxc_partition_function_noalloc", "pxc_set_tile", "pxc_get_tile", "pxc_autotune",
-    "pxc_set_emission", "pxc_cooling_function",
+    "pxc_set_emission", "pxc_cooling_function", "pxc_set_wait_limit",
 ]
 
 # Profile-kernel tile configurations (segment width in grid points), as compiled into the library.
@@ -115,6 +115,7 @@ def load(path: str | None = None):
     L.pxc_set_timing.argtypes = [c_ptr, ctypes.c_int]
     L.pxc_get_timing.argtypes = [c_ptr, c_ptr, c_ptr, c_ptr]
     L.pxc_set_emission.argtypes = [c_ptr, ctypes.c_int]
+    L.pxc_set_wait_limit.argtypes = [c_ptr, c_i64]
     L.pxc_cooling_function.argtypes = [c_ptr, P(pxc_states), P(pxc_transitions), P(pxc_condition), c_i32,
                                        c_ptr, c_ptr, c_ptr]
     L.pxc_set_tile.argtypes = [c_ptr, c_i32, c_i32, c_i32]
@@ -275,6 +276,10 @@ class Workspace:
 
     def set_accumulate(self, on: bool):
         _check(load().pxc_set_accumulate(self.h, int(on)))
+
+    def set_wait_limit(self, cycles: int = 4_000_000_000):
+        """Bound (clock cycles) of the profile kernel's waits for staged records; 0 forces timeouts."""
+        _check(load().pxc_set_wait_limit(self.h, int(cycles)))
 
     def set_emission(self, on: bool):
         """Emission intensities / emission cross sections instead of absorption (workspace mode)."""

@@ -159,7 +159,8 @@ struct ProfP {
   int accumulate;
   int kind;
   unsigned* err;
-  long long spin_limit;
+  long long spin_limit;   // bound of the waits for staged records (clock cycles)
+  long long drain_limit;  // bound of the final wait for copies still in flight after a timeout
 };
 void launch_profile(const ProfP& p, int tile, int grid_ctas, cudaStream_t s);
 int profile_occupancy(int kind, int tile);

@@ -50,7 +50,20 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
 // Bounded wait: true if the phase completed, false after `limit` clock cycles.
+// Non-blocking probe of a phase (try_wait may suspend the thread for a while before failing).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Waits for a phase for at most `limit` clock cycles; a limit of 0 only probes it once.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, long long limit) {
+  if (limit == 0) return mbar_test_wait(bar, parity);
   if (mbar_try_wait(bar, parity)) return true;
   long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
@@ -750,7 +763,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_profile(const ProfP p) {
   __syncthreads();
   if (tid == 0 && abort_sh) {
     for (int b = 0; b < kNB; ++b)
-      if (issued[b] > 0) mbar_wait_bounded(&full[b], (unsigned)((issued[b] - 1) & 1), p.spin_limit);
+      if (issued[b] > 0) mbar_wait_bounded(&full[b], (unsigned)((issued[b] - 1) & 1), p.drain_limit);
   }
 }
 

@@ -183,6 +183,7 @@ struct WsExtra {
   cudaEvent_t ev_copied[2], ev_done[2];
   int occ[kNumKinds][kNumTiles];  // resident profile CTAs per SM for each kind and tile
   int emission;           // emission intensities instead of absorption
+  long long wait_limit;   // bound of the profile kernel's waits for staged records (clock cycles)
   const double* cache_nvib;  // densities the cached Boltzmann table was built with
   int tile[kNumKinds][2];         // tile used for each kind, [single condition, batched]
   // last call
@@ -399,6 +400,7 @@ pxc_status pxc_workspace_create(const pxc_capacity* cap, void* scratch, size_t b
     x->tile[k][0] = 0;
     x->tile[k][1] = kNumTiles - 1;
   }
+  x->wait_limit = kDefaultWaitLimit;
   cudaMemset(ws->err, 0, 256);
   cudaMemset(ws->counters, 0, CNT_N * 8);
   cudaDeviceSynchronize();
@@ -418,6 +420,12 @@ pxc_status pxc_workspace_destroy(pxc_workspace* ws) {
   cudaFreeHost(x->h_cnt);
   delete x;
   free(ws);
+  return PXC_OK;
+}
+
+pxc_status pxc_set_wait_limit(pxc_workspace* ws, int64_t cycles) {
+  if (!ws || cycles < 0) return fail(PXC_ERR_ARG, "set_wait_limit: null workspace or negative limit");
+  X(ws)->wait_limit = cycles;
   return PXC_OK;
 }
 
@@ -643,7 +651,8 @@ pxc_status pxc_cross_section(pxc_workspace* ws, const pxc_states* st, const pxc_
   p.accumulate = ws->accumulate;
   p.kind = pa->kind;
   p.err = ws->err;
-  p.spin_limit = 4000000000ll;  // ~2 s of clock cycles
+  p.spin_limit = x->wait_limit;
+  p.drain_limit = kDefaultWaitLimit;  // copies in flight always land; this bound is never the one reached
   tmark(ws, 2, true, s);
   launch_profile(p, tile, ctas, s);
   tmark(ws, 2, false, s);

@@ -43,7 +43,8 @@ constexpr int kThreadsQ = 256;
 // Profile kernel tiles: segment widths are a runtime choice among the compiled configurations
 // (see kernels_profile.cu); the workspace is sized for the narrowest and the widest.
 constexpr int kNumTiles = 4;
-constexpr int kNumKinds = 8;             // sampled and binned profile kinds (pxc_profile)
+constexpr int kNumKinds = 8;
+constexpr long long kDefaultWaitLimit = 4000000000ll;  // ~2 s of clock cycles             // sampled and binned profile kinds (pxc_profile)
 constexpr int kSegMin = 128;
 constexpr int kSegMax = 2048;
 constexpr int kStageLines = 256;          // lines per TMA stage (two per thread for the constants)
