@@ -104,8 +104,6 @@ void launch_lines(const pxc_transitions* tr, const int32_t* g, int64_t ns, const
 
 void launch_scan_counts(uint32_t* bcount, int64_t nblk, unsigned long long* total, cudaStream_t s);
 
-void launch_compact(const uint64_t* key, int64_t n, const uint32_t* boff, uint64_t* okey, uint32_t* oidx,
-                    cudaStream_t s);
 
 // Sorts (key, idx) pairs of device count *n_dev (<= n_max) by key, stable.  Result
 // ends in buffer 0 (8 passes).

@@ -687,40 +687,6 @@ void launch_scan_counts(uint32_t* bcount, int64_t nblk, unsigned long long* tota
   note_launches(1);
 }
 
-// ------------------------------------------------------------------ stable compaction of kept keys
-__global__ void __launch_bounds__(kThreadsI) k_compact(const uint64_t* __restrict__ key, int64_t n,
-                                                       const uint32_t* __restrict__ boff, uint64_t* __restrict__ okey,
-                                                       uint32_t* __restrict__ oidx) {
-  __shared__ uint32_t wsum[kThreadsI / 32];
-  const int64_t base = (int64_t)blockIdx.x * kLinesPerBlockI;
-  uint32_t run = boff[blockIdx.x];
-  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int k = 0; k < kLinesPerBlockI / kThreadsI; ++k) {
-    int64_t t = base + k * kThreadsI + threadIdx.x;
-    uint64_t kk = t < n ? key[t] : kSentinelKey;
-    bool keep = kk != kSentinelKey;
-    unsigned m = __ballot_sync(0xffffffffu, keep);
-    if (lane == 0) wsum[w] = __popc(m);
-    __syncthreads();
-    uint32_t before = 0, tot = 0;
-    for (int i = 0; i < kThreadsI / 32; ++i) { before += i < w ? wsum[i] : 0; tot += wsum[i]; }
-    if (keep) {
-      uint32_t p = run + before + __popc(m & ((1u << lane) - 1u));
-      okey[p] = kk;
-      oidx[p] = (uint32_t)(t - 0);
-    }
-    run += tot;
-    __syncthreads();
-  }
-}
-
-void launch_compact(const uint64_t* key, int64_t n, const uint32_t* boff, uint64_t* okey, uint32_t* oidx,
-                    cudaStream_t s) {
-  int64_t nblk = (n + kLinesPerBlockI - 1) / kLinesPerBlockI;
-  if (nblk == 0) return;
-  k_compact<<<(unsigned)nblk, kThreadsI, 0, s>>>(key, n, boff, okey, oidx);
-  note_launches(1);
-}
 
 // ------------------------------------------------------------------ LSD radix sort, 8 passes of 8 bits
 // Pass: per-tile digit histogram -> per-digit exclusive scan over tiles -> stable scatter.

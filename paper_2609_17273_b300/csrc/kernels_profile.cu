@@ -387,12 +387,6 @@ __device__ __forceinline__ int line_class(const LineC& c, int a) {
   return (c.lo <= a && c.hi >= b) ? 1 : 2;
 }
 
-template <int KIND>
-__device__ __forceinline__ float eval_general(float x, const LineC& c) {
-  if (KIND == PXC_VOIGT) return c.Kc * w4_re(x, c.y);
-  if (KIND == PXC_LORENTZ) return c.K * frcp(fmaf(x, x, c.B1));
-  return c.K * fex2(-(x * x));
-}
 
 // Branch-free evaluation of one line at the lane's PTS points (fast class); lk[k] = lane + 32 k.
 template <int KIND, int PTS>
