@@ -42,7 +42,7 @@ L2_BYTES = 126 * 2 ** 20
 # DRAM traffic per profile-kernel launch from the committed ncu capture, valid only for
 # the kernel source it was taken on (sha256 prefix of kernels_profile.cu).
 # Both come from an ncu capture of the 2e7-line case, scaled x5 to one 1e8-line launch.
-NCU_TRAFFIC = {("profile", "e9ce053a4568a9ab"): 90473960, ("intensity", "fb308f3eb66b492b"): 9564512080}
+NCU_TRAFFIC = {("profile", "d0f409663eef7981"): 90473960, ("intensity", "4e40566b8da31649"): 9564512080}
 
 
 def _src_hash(rel):
