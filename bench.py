@@ -126,6 +126,17 @@ def replica_rate(units_per_rank: float, steps: int, world: int, ms_max: float) -
 
 # ----------------------------------------------------------------------------- reference arm (oracle)
 
+def _cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def oracle_sample_rate(w, E, g, n_lines, threads):
     """Oracle throughput (evals/s) on the first n_lines transitions of the workload, full grid."""
     import numpy as np
@@ -397,7 +408,14 @@ def main_pxc(args):
         n = calibrate_sample(w, E, g, threads, args.ref_step_s)
         ev, nl, dt = oracle_sample_rate(w, E, g, n, threads)
         out["cpu_baseline"] = {"value": ev / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-                               "sample": f"first {nl} of {w.n_trans} transitions, full grid, {dt:.1f} s"}
+                               "sample": f"first {nl} of {w.n_trans} transitions, full grid, {dt:.1f} s",
+                               "cpu": _cpu_model()}
+        # the same oracle on one thread, on a sample a `threads`-th the size
+        import oracle
+        oracle.set_threads(1)
+        ev1, nl1, dt1 = oracle_sample_rate(w, E, g, max(1000, n // max(threads, 1)), 1)
+        oracle.set_threads(threads)
+        out["cpu_baseline"]["one_thread"] = {"value": ev1 / dt1, "sample": f"first {nl1} transitions, {dt1:.1f} s"}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

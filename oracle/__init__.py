@@ -46,6 +46,7 @@ def _load():
         L = ctypes.CDLL(_LIB)
         P, i64, dbl, cint = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
         L.orc_c2.restype = dbl
+        L.orc_set_threads.argtypes = [cint]
         L.orc_faddeeva.argtypes = [i64, P, P, P, P]
         L.orc_profile.argtypes = [cint, i64, P, dbl, dbl, P, P, P]
         L.orc_partition.argtypes = [P, P, P, i64, dbl, dbl, P]
@@ -88,6 +89,11 @@ class OracleError(RuntimeError):
 def _chk(code):
     if code != 0:
         raise OracleError(code)
+
+
+def set_threads(n: int) -> None:
+    """Number of OpenMP threads the oracle's parallel loops use."""
+    _load().orc_set_threads(int(n))
 
 
 def c2() -> float:

@@ -65,6 +65,7 @@
 #undef I
 #define CI _Complex_I
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -85,6 +86,9 @@ enum { ORC_GAUSS_DOPPLER = 0, ORC_GAUSS_HWHM = 1, ORC_LORENTZ = 2, ORC_VOIGT = 3
 enum { ORC_BINNED = 4 };
 
 double orc_c2(void) { return ORC_H * ORC_C / ORC_KB; }
+
+/* Threads of the OpenMP loops (the CPU-baseline timing reports all cores and one). */
+void orc_set_threads(int n) { if (n > 0) omp_set_num_threads(n); }
 
 /* ---------------------------------------------------------------------------
  * Faddeeva function w(z), Im z >= 0.
