@@ -81,3 +81,25 @@ def test_binding_fails_loudly_without_library(tmp_path):
             pxc.load(str(tmp_path / "missing.so"))
     finally:
         pxc._lib = saved
+
+
+def test_null_workspace_and_bad_arguments_are_rejected_on_the_host(lib):
+    # every entry point checks its arguments before touching the device
+    import paper_2609_17273_b300 as pxc
+    L = pxc.load()
+    assert L.pxc_set_tile(None, 3, 0, 0) == 1
+    assert L.pxc_get_tile(None, 3, 0, None) == 1
+    assert L.pxc_set_emission(None, 1) == 1
+    assert L.pxc_set_wait_limit(None, 10) == 1
+    assert L.pxc_set_accumulate(None, 1) == 1
+    assert L.pxc_cooling_function(None, None, None, None, 1, None, None, None) == 1
+    assert L.pxc_cross_section(None, None, None, None, 1, None, None, 0.0, None, None, None) == 1
+    assert L.pxc_partition_function_noalloc(None, None, 1, None, None, None, None) == 1
+    cond = (pxc.pxc_condition * 65)()
+    st = pxc.pxc_states(ctypes.c_void_p(16), ctypes.c_void_p(16), None, 10, None)
+    for i in range(65):
+        cond[i] = pxc.pxc_condition(300.0, 0.0, 1.0)
+    # more conditions than the fixed scratch holds: a capacity error, still on the host
+    assert L.pxc_partition_function_noalloc(ctypes.byref(st), cond, 65, ctypes.c_void_p(16), None, None,
+                                            None) == 7
+    assert b"64" in L.pxc_last_error()
