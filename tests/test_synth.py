@@ -4,6 +4,7 @@ import subprocess
 import sys
 
 import numpy as np
+import pytest
 
 import synth
 
@@ -54,3 +55,15 @@ def test_thread_count_independent():
         outs.append(subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
                                    check=True).stdout.strip())
     assert outs[0] == outs[1]
+
+
+def test_vibronic_densities_are_per_manifold_normalised_and_seeded():
+    w = synth.workload("nlte_1e7")
+    d = w.vib_densities()
+    assert d.shape == (w.n_states,) and d.dtype == np.float64
+    per_v = d.reshape(w.nv, w.nJ)
+    assert np.all(per_v == per_v[:, :1])                     # one weight per vibrational manifold
+    assert per_v[:, 0].sum() == pytest.approx(1.0, rel=1e-14)
+    assert np.all(per_v[:, 0] > 0) and np.array_equal(d, w.vib_densities())
+    with pytest.raises(ValueError):
+        synth.workload("voigt_1e9").vib_densities()
