@@ -21,7 +21,7 @@
  *   W(T)                 Eq. (cf), cooling function  [reading R17 below for non-LTE]
  *   binned profiles      Table (profile), binned Doppler / Gaussian / Lorentzian / Voigt [R19]
  *
- * Readings where the text is silent or garbled (each also listed in the design doc):
+ * Readings where the text is silent or garbled:
  *   R7  nu = E' - E''; lines with nu <= 0 are dropped (nu = 0 would divide by zero).
  *   R8  window of grid indices: i_lo = ceil((nu - cut - nu_min)/dnu),
  *       i_hi = floor((nu + cut - nu_min)/dnu), plain IEEE double, no FMA,
