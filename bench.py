@@ -15,8 +15,8 @@ binning, Voigt accumulation).  Inputs are synthetic and seeded.
   extras: the batched 200-condition opacity table against 200 sequential calls,
           and forward+backward against forward on the two-temperature list
 
-`--impl reference` times the FP64 oracle (the reference arm of this build) on
-bounded samples of the same workload on the host cores.
+`--impl reference` times the FP64 oracle (the reference arm: there is no other
+implementation to install) on bounded samples of the same workload on the host cores.
 """
 from __future__ import annotations
 
