@@ -11,6 +11,13 @@ enum { CNT_QUEUE = 0, CNT_ITEMS = 1, CNT_KEPT = 2, CNT_NONZERO = 3, CNT_EVALS = 
        CNT_ITEMS_RAW = 7, CNT_N = 16 };
 
 
+// Host-side argument checks and per-condition constants shared by every entry point
+// (pxc_api.cu); on failure they set the thread-local message and return the status.
+struct SlotP;
+pxc_status validate_states(const pxc_states* st);
+pxc_status validate_condition(const pxc_condition& c, const pxc_states* st);
+void set_last_error(const char* msg);
+
 // Kernel launches issued by the library since load (all workspaces, all threads).
 void note_launches(int n);
 int64_t launches_total();
@@ -28,6 +35,7 @@ struct SlotP {                    // one temperature pair
   double c2_Tv;                   // c2 / T_vib, 0 for LTE
   double T, T_vib;                // T (T_rot) and T_vib (0 for LTE)
 };
+SlotP slot_constants(const pxc_condition& c);
 
 // Partial sums per (block, slot): Q, and the moments for dQ/dT, dQ/dT_vib and the cooling function.
 constexpr int kQMoments = 4;

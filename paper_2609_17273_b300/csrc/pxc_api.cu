@@ -349,6 +349,11 @@ int profile_ctas(pxc_workspace* ws, int kind, int tile) {
 
 namespace pxc {
 void set_last_error(const char* msg) { snprintf(g_msg, sizeof g_msg, "%s", msg); }
+// The argument checks and per-condition constants of the workspace entry points, shared with
+// the allocation-free partition function so that both accept exactly the same inputs.
+pxc_status validate_states(const pxc_states* st) { return check_states(st); }
+pxc_status validate_condition(const pxc_condition& c, const pxc_states* st) { return check_cond(c, false, st); }
+SlotP slot_constants(const pxc_condition& c) { return make_slot(c); }
 }  // namespace pxc
 
 extern "C" {

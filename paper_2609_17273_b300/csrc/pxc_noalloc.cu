@@ -72,37 +72,27 @@ double* g_addr[kMaxDevices] = {};
 
 }  // namespace
 
-namespace pxc {
-void set_last_error(const char* msg);  // defined with pxc_last_error
-}
-
 extern "C" pxc_status pxc_partition_function_noalloc(const pxc_states* states, const pxc_condition* c, int32_t n_c,
                                                      double* Q_out, double* dQ_out, int32_t* status_out,
                                                      cudaStream_t stream) {
-  if (!states || !c || !Q_out || n_c < 1 || states->n < 0 ||
-      (states->n > 0 && (!states->E || !states->g))) {
+  if (!c || !Q_out || n_c < 1) {
     pxc::set_last_error("partition_function_noalloc: bad arguments");
     return PXC_ERR_ARG;
   }
+  // the same checks as pxc_partition_function: states (null pointers, n < 0, more than 2^31-1
+  // states) and every condition (T finite and > 0, T_vib finite, E_vib present for T_vib > 0,
+  // vibronic densities only with E_vib and without T_vib)
+  pxc_status r = pxc::validate_states(states);
+  if (r) return r;
   if (n_c > kNoAllocConditions) {
     pxc::set_last_error("partition_function_noalloc: more than 64 conditions");
     return PXC_ERR_CAPACITY;
   }
   NoAllocConds conds{};
   conds.n = n_c;
-  const double c2 = pxc::kH * pxc::kC / pxc::kKB;
   for (int i = 0; i < n_c; ++i) {
-    if (!(c[i].T > 0.0) || (c[i].T_vib > 0.0 && !states->E_vib) ||
-        (states->n_vib && (!states->E_vib || c[i].T_vib > 0.0))) {
-      pxc::set_last_error("partition_function_noalloc: bad condition (T <= 0, T_vib > 0 without E_vib, or "
-                          "vibronic densities without E_vib or with T_vib > 0)");
-      return PXC_ERR_ARG;
-    }
-    pxc::SlotP& sp = conds.s[i];
-    sp.c2_T = c2 / c[i].T;
-    sp.c2_Tv = c[i].T_vib > 0.0 ? c2 / c[i].T_vib : 0.0;
-    sp.T = c[i].T;
-    sp.T_vib = c[i].T_vib > 0.0 ? c[i].T_vib : 0.0;
+    if ((r = pxc::validate_condition(c[i], states))) return r;
+    conds.s[i] = pxc::slot_constants(c[i]);
   }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {

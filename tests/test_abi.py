@@ -103,3 +103,27 @@ def test_null_workspace_and_bad_arguments_are_rejected_on_the_host(lib):
     assert L.pxc_partition_function_noalloc(ctypes.byref(st), cond, 65, ctypes.c_void_p(16), None, None,
                                             None) == 7
     assert b"64" in L.pxc_last_error()
+
+
+def test_noalloc_rejects_what_the_workspace_entry_point_rejects(lib):
+    # the allocation-free partition function runs the same host-side checks as
+    # pxc_partition_function, before any CUDA call
+    import paper_2609_17273_b300 as pxc
+    L = pxc.load()
+    st = pxc.pxc_states(ctypes.c_void_p(16), ctypes.c_void_p(16), None, 10, None)
+    Q = ctypes.c_void_p(16)
+    for T, Tv in [(float("inf"), 0.0), (float("nan"), 0.0), (0.0, 0.0), (-300.0, 0.0), (300.0, float("nan")),
+                  (300.0, float("inf")), (300.0, 2500.0)]:   # the last needs E_vib
+        cond = pxc.pxc_condition(T, Tv, 1.0)
+        assert L.pxc_partition_function_noalloc(ctypes.byref(st), ctypes.byref(cond), 1, Q, None, None, None) == 1, \
+            (T, Tv)
+    # vibronic densities need E_vib and exclude T_vib
+    dens = pxc.pxc_states(ctypes.c_void_p(16), ctypes.c_void_p(16), None, 10, ctypes.c_void_p(16))
+    cond = pxc.pxc_condition(300.0, 0.0, 1.0)
+    assert L.pxc_partition_function_noalloc(ctypes.byref(dens), ctypes.byref(cond), 1, Q, None, None, None) == 1
+    # more states than the 32-bit state ids can address
+    big = pxc.pxc_states(ctypes.c_void_p(16), ctypes.c_void_p(16), None, 2 ** 31, None)
+    assert L.pxc_partition_function_noalloc(ctypes.byref(big), ctypes.byref(cond), 1, Q, None, None, None) == 1
+    assert b"2^31" in L.pxc_last_error()
+    neg = pxc.pxc_states(ctypes.c_void_p(16), ctypes.c_void_p(16), None, -1, None)
+    assert L.pxc_partition_function_noalloc(ctypes.byref(neg), ctypes.byref(cond), 1, Q, None, None, None) == 1
