@@ -238,7 +238,7 @@ __device__ __forceinline__ float w4_re(float x, float y) {
 
 struct __align__(16) LineC {
   // fast-path constants, first so that two 16-byte loads fetch them:
-  //   Voigt:   a = x at lane 0 of the owning warp, b = step, B1 = 2y^2 - 1, d = A2
+  //   Voigt:   a = x at lane 0 of the owning warp, b = step, B1 = c1 = y^2 - 1/2, d = e = 2 y^2
   //   others:  a = wbase - pf (exact integer), b = step, B1 = gamma^2 (Lorentz) or 0, d = nfs
   float a, b, B1, d;
   float K, KA, y, Kc;          // amplitudes (K: fast/region I, Kc: general path), y (Voigt) or gamma
@@ -331,12 +331,14 @@ __device__ __forceinline__ void line_constants(const int4 p4, const float2 pr, c
       c.y = y;
       c.step = dnu_f * cc;
       c.nfs = -f * c.step;
-      const float A = 0.5f + y * y;
-      c.B1 = 2.f * y * y - 1.f;
-      c.d = A * A;
+      // region I: Re w = y (A + x^2) / (sqrt(pi) ((A - x^2)^2 + 4 x^2 y^2)), A = 1/2 + y^2, written
+      // with v = x^2 + c1, c1 = y^2 - 1/2, as y (v + 1) / (sqrt(pi) (v^2 + e)), e = 2 y^2
+      // (the denominator is the same quartic: (x^2 + c1)^2 + 2 y^2 = x^4 + (2y^2 - 1) x^2 + A^2)
+      c.B1 = fmaf(y, y, -0.5f);
+      c.d = 2.f * y * y;
       c.Kc = is * cc * kInvSqrtPi;
       c.K = c.Kc * y * kInvSqrtPi;
-      c.KA = c.K * A;
+      c.KA = c.K;
       reach = fmaxf(15.f - y, 0.f) * frcp(c.step) * 1.0001f;
       c.a = fmaf((float)wbase - c.pf, c.step, c.nfs);
       c.b = c.step;
@@ -395,15 +397,14 @@ __device__ __forceinline__ void eval_fast(const LineC& c, const float* lk, float
   const float4 f0 = *reinterpret_cast<const float4*>(&c.a);  // a, b, B1, d
   const float K = c.K;
   if (KIND == PXC_VOIGT) {
-    // far wing, W4 region I: Re w = y (A + x^2) / (sqrt(pi) ((A - x^2)^2 + 4 x^2 y^2)), A = 1/2 + y^2;
-    // no point of this warp is near the centre, so x = x(lane 0) + m step keeps full relative accuracy
-    const float KA = c.KA;
+    // far wing, W4 region I: K (v + 1) / (v^2 + e), v = x^2 + c1 (five FP32 FMAs and one MUFU
+    // reciprocal per point); no point of this warp is near the centre, so x = x(lane 0) + m step
+    // keeps full relative accuracy
 #pragma unroll
     for (int k = 0; k < PTS; ++k) {
       const float x = fmaf(lk[k], f0.y, f0.x);
-      const float x2 = x * x;
-      const float den = fmaf(x2, x2 + f0.z, f0.w);
-      acc[k] = fmaf(fmaf(x2, K, KA), frcp(den), acc[k]);
+      const float v = fmaf(x, x, f0.z);
+      acc[k] = fmaf(fmaf(v, K, K), frcp(fmaf(v, v, f0.w)), acc[k]);
     }
   } else {
     // the line centre may lie among these points: x from the exact integer offset
@@ -426,9 +427,9 @@ __device__ __forceinline__ void eval_fast2(const LineC& c, const LineC& e, const
 #pragma unroll
     for (int k = 0; k < PTS; ++k) {
       const float x = fmaf(lk[k], a0.y, a0.x), y = fmaf(lk[k], b0.y, b0.x);
-      const float x2 = x * x, y2 = y * y;
-      const float ra = frcp(fmaf(x2, x2 + a0.z, a0.w)), rb = frcp(fmaf(y2, y2 + b0.z, b0.w));
-      acc[k] = fmaf(fmaf(x2, a1.x, a1.y), ra, fmaf(fmaf(y2, b1.x, b1.y), rb, acc[k]));
+      const float u = fmaf(x, x, a0.z), v = fmaf(y, y, b0.z);
+      const float ra = frcp(fmaf(u, u, a0.w)), rb = frcp(fmaf(v, v, b0.w));
+      acc[k] = fmaf(fmaf(u, a1.x, a1.x), ra, fmaf(fmaf(v, b1.x, b1.x), rb, acc[k]));
     }
   } else {
     eval_fast<KIND, PTS>(c, lk, acc);
@@ -500,9 +501,8 @@ __device__ __forceinline__ void eval_fastmask(const LineC& c, int wbase, int lan
 #pragma unroll
     for (int k = 0; k < PTS; ++k) {
       const float x = fmaf((float)k, s32, x0);
-      const float x2 = x * x;
-      const float den = fmaf(x2, x2 + c.B1, c.d);
-      const float v = fmaf(x2, c.K, c.KA) * frcp(den);
+      const float u = fmaf(x, x, c.B1);
+      const float v = fmaf(u, c.K, c.K) * frcp(fmaf(u, u, c.d));
       acc[k] += (unsigned)(rel0 + 32 * k) <= span ? v : 0.f;
     }
   } else {
@@ -581,8 +581,8 @@ __device__ __forceinline__ void eval_slow(const LineC& c, int wbase, int lane, c
       // the whole block is in region I (uniform branch): the fast-path formula (measured to pay
       // off for wide warps only; narrow ones rarely have such blocks among their slow lines)
       const float x = fmaf(lk[k], c.b, c.a);
-      const float x2 = x * x;
-      const float v = fmaf(x2, c.K, c.KA) * frcp(fmaf(x2, x2 + c.B1, c.d));
+      const float u = fmaf(x, x, c.B1);
+      const float v = fmaf(u, c.K, c.K) * frcp(fmaf(u, u, c.d));
       acc[k] += in ? v : 0.f;
       continue;
     }
@@ -590,7 +590,8 @@ __device__ __forceinline__ void eval_slow(const LineC& c, int wbase, int lane, c
     float v;
     const float x2 = x * x;
     if (fabsf(x) + c.y >= 15.f) {
-      v = fmaf(x2, c.K, c.KA) * frcp(fmaf(x2, x2 + c.B1, c.d));
+      const float u = fmaf(x, x, c.B1);
+      v = fmaf(u, c.K, c.K) * frcp(fmaf(u, u, c.d));
     } else if (fabsf(x) + c.y >= 5.5f) {
       const float N = fmaf(fmaf(fmaf(r.n3, x2, r.n2), x2, r.n1), x2, r.n0);
       const float D = fmaf(fmaf(fmaf(x2 + r.d3, x2, r.d2), x2, r.d1), x2, r.d0);
