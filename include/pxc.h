@@ -174,6 +174,22 @@ pxc_status pxc_set_accumulate(pxc_workspace* ws, int on);
  * exponent handling.  pxc_cross_section_backward is absorption-only (PXC_ERR_ARG here). */
 pxc_status pxc_set_emission(pxc_workspace* ws, int on);
 
+/* CUDA-graph replay of pxc_cross_section (Sec. 4.4: a batched (T, P) table is re-evaluated with
+ * the same preprocessing; the many small launches of the intensity, sort and binning passes are
+ * then replayed as one graph).  When on, each distinct call -- the same pointers, sizes,
+ * conditions, grid, profile arguments, threshold and outputs, and the same workspace modes and
+ * tile -- is captured into a CUDA graph the first time it is made and replayed by later identical
+ * calls (the device data behind the pointers may change between calls; the graph reads it
+ * afresh).  Up to 8 graphs are kept per workspace, the least recently used dropped first.  The
+ * capture runs on a stream the workspace owns, so the caller's stream may be the legacy default
+ * stream; the first call of a shape therefore costs a capture and an instantiation.  Accumulate
+ * mode is never captured (its result depends on the workspace's running state), and pass timing
+ * (pxc_set_timing) is not recorded for replays.  Turning graphs off frees the cached graphs.
+ * No counterpart in the paper. */
+pxc_status pxc_set_graphs(pxc_workspace* ws, int on);
+/* Captures made, replays made and graphs cached by this workspace (each pointer nullable). */
+pxc_status pxc_graph_stats(pxc_workspace* ws, int64_t* captures, int64_t* replays, int32_t* cached);
+
 /* Bound, in SM clock cycles, of the profile kernel's waits for line records staged by bulk
  * copies (default 4e9, about 2 s).  A wait that runs out sets PXC_ERR_TIMEOUT (returned by
  * pxc_sync_status); its CTA lets the copies it issued land and returns, so the context and the
@@ -345,6 +361,20 @@ pxc_status pxc_cooling_function(pxc_workspace* ws, const pxc_states* states, con
 pxc_status pxc_partition_function_noalloc(const pxc_states* states, const pxc_condition* c, int32_t n_c,
                                           double* Q_out, double* dQ_out, int32_t* status_out,
                                           cudaStream_t stream);
+
+/* Instruction-throughput microbenchmark of the current device (no counterpart in the paper;
+ * the profile pass of Eq. xsec is bound by these pipes, so its roofline is stated against
+ * rates measured on the chip).  Runs one full wave of four kernels on `stream` and synchronises:
+ *   host_out[0] FP32 FMA results per SM per clock cycle
+ *   host_out[1] MUFU reciprocal (rcp.approx.ftz.f32) results per SM per clock cycle
+ *   host_out[2] MUFU exp2 (ex2.approx.ftz.f32) results per SM per clock cycle
+ *   host_out[3] far-wing Voigt evaluations (5 FP32 FMAs + 1 reciprocal each) per SM per clock
+ *   host_out[4..7] the same four rates per second at the clock the device ran (CUDA events).
+ * Per-clock rates come from the SM cycle counter of every CTA, so they do not depend on the
+ * clock frequency.  dev_buf: caller device memory of pxc_pipe_rates_buffer_bytes() bytes.
+ * PXC_ERR_ARG for a null or short buffer, PXC_ERR_CUDA if a kernel fails. */
+size_t pxc_pipe_rates_buffer_bytes(void);
+pxc_status pxc_pipe_rates(void* dev_buf, size_t bytes, double* host_out, cudaStream_t stream);
 
 #ifdef __cplusplus
 }

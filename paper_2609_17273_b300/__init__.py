@@ -75,7 +75,8 @@ ABI_FUNCTIONS = [
     "pxc_cross_section_backward", "pxc_get_stats", "pxc_get_binning", "pxc_stream_buffer_bytes",
     "pxc_cross_section_streamed", "pxc_kernel_launches", "pxc_set_timing", "pxc_get_timing",
     "pxc_partition_function_noalloc", "pxc_set_tile", "pxc_get_tile", "pxc_autotune",
-    "pxc_set_emission", "pxc_cooling_function", "pxc_set_wait_limit",
+    "pxc_set_emission", "pxc_cooling_function", "pxc_set_wait_limit", "pxc_pipe_rates_buffer_bytes",
+    "pxc_pipe_rates", "pxc_set_graphs", "pxc_graph_stats",
 ]
 
 # Profile-kernel tile configurations (segment width in grid points), as compiled into the library.
@@ -116,6 +117,8 @@ def load(path: str | None = None):
     L.pxc_get_timing.argtypes = [c_ptr, c_ptr, c_ptr, c_ptr]
     L.pxc_set_emission.argtypes = [c_ptr, ctypes.c_int]
     L.pxc_set_wait_limit.argtypes = [c_ptr, c_i64]
+    L.pxc_set_graphs.argtypes = [c_ptr, ctypes.c_int]
+    L.pxc_graph_stats.argtypes = [c_ptr, P(c_i64), P(c_i64), P(c_i32)]
     L.pxc_cooling_function.argtypes = [c_ptr, P(pxc_states), P(pxc_transitions), P(pxc_condition), c_i32,
                                        c_ptr, c_ptr, c_ptr]
     L.pxc_set_tile.argtypes = [c_ptr, c_i32, c_i32, c_i32]
@@ -127,9 +130,13 @@ def load(path: str | None = None):
     L.pxc_cross_section_streamed.argtypes = [c_ptr, P(pxc_states), c_ptr, c_ptr, c_ptr, c_i32, c_ptr, c_ptr, c_i64,
                                              P(pxc_condition), P(pxc_grid), P(pxc_profile_args), c_dbl,
                                              c_ptr, c_ptr, ctypes.c_size_t, c_ptr, c_ptr, c_ptr]
+    L.pxc_pipe_rates_buffer_bytes.argtypes = []
+    L.pxc_pipe_rates_buffer_bytes.restype = ctypes.c_size_t
+    L.pxc_pipe_rates.argtypes = [c_ptr, ctypes.c_size_t, c_ptr, c_ptr]
     for name in ABI_FUNCTIONS:
         fn = getattr(L, name)
-        if name not in ("pxc_last_error", "pxc_stream_buffer_bytes", "pxc_kernel_launches"):
+        if name not in ("pxc_last_error", "pxc_stream_buffer_bytes", "pxc_kernel_launches",
+                        "pxc_pipe_rates_buffer_bytes"):
             fn.restype = ctypes.c_int
     _lib = L
     return L
@@ -285,6 +292,15 @@ class Workspace:
         """Emission intensities / emission cross sections instead of absorption (workspace mode)."""
         _check(load().pxc_set_emission(self.h, int(on)))
 
+    def set_graphs(self, on: bool):
+        """Capture distinct pxc_cross_section calls into CUDA graphs and replay identical ones."""
+        _check(load().pxc_set_graphs(self.h, int(on)))
+
+    def graph_stats(self) -> dict:
+        cap, rep, cached = c_i64(0), c_i64(0), c_i32(0)
+        _check(load().pxc_graph_stats(self.h, ctypes.byref(cap), ctypes.byref(rep), ctypes.byref(cached)))
+        return {"captures": int(cap.value), "replays": int(rep.value), "cached": int(cached.value)}
+
     def set_tile(self, kind: int, batched: bool, tile: int):
         """Profile-kernel tile for this kind and for single-condition (batched=False) or batched calls."""
         _check(load().pxc_set_tile(self.h, int(kind), int(bool(batched)), int(tile)))
@@ -293,6 +309,19 @@ class Workspace:
         t = c_i32(0)
         _check(load().pxc_get_tile(self.h, int(kind), int(bool(batched)), ctypes.byref(t)))
         return int(t.value)
+
+
+def pxc_pipe_rates(stream=None) -> dict:
+    """Measured FP32 FMA, MUFU rcp / ex2 and far-wing Voigt evaluation rates of the current device:
+    per SM per clock cycle and per second (include/pxc.h, pxc_pipe_rates)."""
+    L = load()
+    nb = L.pxc_pipe_rates_buffer_bytes()
+    buf = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    out = (ctypes.c_double * 8)()
+    _check(L.pxc_pipe_rates(_ptr(buf), nb, out, _stream(stream)))
+    names = ("fma", "rcp", "ex2", "voigt_far_eval")
+    return {"per_sm_per_clk": {n: out[i] for i, n in enumerate(names)},
+            "per_s": {n: out[4 + i] for i, n in enumerate(names)}}
 
 
 def pxc_partition_function(ws: Workspace, states: States, conds, stream=None):

@@ -174,6 +174,17 @@ GridP make_gridp(const pxc_grid& g, double cut) {
 template <typename T>
 T* at(pxc_workspace* ws, size_t off) { return reinterpret_cast<T*>(ws->base + off); }
 
+// One captured pxc_cross_section: the call's key (every pointer and value it depends on), the
+// instantiated graph, the kernels it holds and the host-side bookkeeping of the call.
+struct GraphEntry {
+  std::vector<unsigned char> key;
+  cudaGraphExec_t exec;
+  int64_t kernels;
+  int64_t last_nseg;
+  int last_seg, last_tile, last_nc;
+};
+constexpr size_t kGraphCacheMax = 8;
+
 struct WsExtra {
   Layout L;
   void* h_params;        // pinned host staging of small parameter blocks
@@ -195,6 +206,12 @@ struct WsExtra {
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, int>> ev_used;  // (pass, index of the start event)
   size_t ev_next;
+  // CUDA-graph replay of pxc_cross_section (pxc_set_graphs)
+  int graphs;
+  int capturing;
+  cudaStream_t cap_stream;
+  std::vector<GraphEntry> gcache;  // most recently used last
+  int64_t graph_hits, graph_captures;
 };
 
 // Records a timing event for `pass` (start or end) when timing is on.
@@ -331,7 +348,7 @@ pxc_status front_plain(pxc_workspace* ws, const pxc_states* st, const pxc_transi
 
 void tmark(pxc_workspace* ws, int pass, bool start, cudaStream_t s) {
   WsExtra* x = X(ws);
-  if (!x->timing) return;
+  if (!x->timing || x->capturing) return;
   if (x->ev_next + 1 >= x->ev_pool.size()) return;  // pool exhausted: stop recording
   cudaEvent_t e = x->ev_pool[x->ev_next];
   if (start) x->ev_used.push_back({pass, (int)x->ev_next});
@@ -406,6 +423,7 @@ pxc_status pxc_workspace_create(const pxc_capacity* cap, void* scratch, size_t b
     x->tile[k][1] = kNumTiles - 1;
   }
   x->wait_limit = kDefaultWaitLimit;
+  cudaStreamCreateWithFlags(&x->cap_stream, cudaStreamNonBlocking);
   cudaMemset(ws->err, 0, 256);
   cudaMemset(ws->counters, 0, CNT_N * 8);
   cudaDeviceSynchronize();
@@ -420,6 +438,8 @@ pxc_status pxc_workspace_destroy(pxc_workspace* ws) {
   cudaStreamDestroy(x->copy_stream);
   for (int i = 0; i < 2; ++i) { cudaEventDestroy(x->ev_copied[i]); cudaEventDestroy(x->ev_done[i]); }
   for (auto& e : x->ev_pool) cudaEventDestroy(e);
+  for (auto& g : x->gcache) cudaGraphExecDestroy(g.exec);
+  cudaStreamDestroy(x->cap_stream);
   cudaFreeHost(x->h_params);
   cudaFreeHost(x->h_err);
   cudaFreeHost(x->h_cnt);
@@ -551,9 +571,14 @@ pxc_status pxc_line_intensities(pxc_workspace* ws, const pxc_states* st, const p
   return cuda_check("line_intensities");
 }
 
-pxc_status pxc_cross_section(pxc_workspace* ws, const pxc_states* st, const pxc_transitions* tr,
-                             const pxc_condition* c, int32_t n_c, const pxc_grid* grid, const pxc_profile_args* pa,
-                             double threshold, float* sigma_out, int32_t* sigma_exp_out, cudaStream_t s) {
+}  // extern "C"
+
+namespace {
+
+pxc_status cross_section_direct(pxc_workspace* ws, const pxc_states* st, const pxc_transitions* tr,
+                                const pxc_condition* c, int32_t n_c, const pxc_grid* grid,
+                                const pxc_profile_args* pa, double threshold, float* sigma_out,
+                                int32_t* sigma_exp_out, cudaStream_t s) {
   if (!ws || !c || n_c < 1 || !sigma_out || !sigma_exp_out) return fail(PXC_ERR_ARG, "cross_section: bad arguments");
   pxc_status r;
   if ((r = check_states(st)) || (r = check_trans(tr)) || (r = check_prof(pa, tr))) return r;
@@ -669,6 +694,133 @@ pxc_status pxc_cross_section(pxc_workspace* ws, const pxc_states* st, const pxc_
   x->last_tile = tile;
   ws->last_nc = n_c;
   return cuda_check("cross_section");
+}
+
+template <typename T>
+void put(std::vector<unsigned char>& k, const T& v) {
+  const unsigned char* p = reinterpret_cast<const unsigned char*>(&v);
+  k.insert(k.end(), p, p + sizeof(T));
+}
+
+// Everything a captured call depends on besides the contents of device memory: the pointers and
+// sizes of every array, the conditions, grid, profile and threshold, and the workspace's modes.
+std::vector<unsigned char> graph_key(pxc_workspace* ws, const pxc_states* st, const pxc_transitions* tr,
+                                     const pxc_condition* c, int32_t n_c, const pxc_grid* grid,
+                                     const pxc_profile_args* pa, double threshold, float* sigma_out,
+                                     int32_t* sigma_exp_out, cudaStream_t s) {
+  WsExtra* x = X(ws);
+  std::vector<unsigned char> k;
+  k.reserve(256 + 24 * (size_t)n_c);
+  put(k, st->E); put(k, st->g); put(k, st->E_vib); put(k, st->n); put(k, st->n_vib);
+  put(k, tr->upper); put(k, tr->lower); put(k, tr->A); put(k, tr->A_is_f32); put(k, tr->n);
+  put(k, n_c);
+  for (int i = 0; i < n_c; ++i) { put(k, c[i].T); put(k, c[i].T_vib); put(k, c[i].P); }
+  put(k, grid->nu_min); put(k, grid->dnu); put(k, grid->n);
+  put(k, pa->kind); put(k, pa->cutoff); put(k, pa->mass_da); put(k, pa->hwhm); put(k, pa->gamma_ref);
+  put(k, pa->n_T); put(k, pa->T_ref);
+  put(k, threshold); put(k, sigma_out); put(k, sigma_exp_out);
+  const int kind = pa->kind >= 0 && pa->kind < kNumKinds ? pa->kind : 0;
+  put(k, x->tile[kind][n_c > 1 ? 1 : 0]); put(k, x->emission); put(k, x->wait_limit);
+  (void)s;
+  return k;
+}
+
+pxc_status launch_entry(pxc_workspace* ws, GraphEntry& g, cudaStream_t s) {
+  WsExtra* x = X(ws);
+  if (cudaGraphLaunch(g.exec, s) != cudaSuccess) return cuda_check("cross_section graph launch");
+  note_launches((int)g.kernels);
+  x->last_nseg = g.last_nseg;
+  x->last_seg = g.last_seg;
+  x->last_tile = g.last_tile;
+  ws->last_nc = g.last_nc;
+  return cuda_check("cross_section graph launch");
+}
+
+}  // namespace
+
+extern "C" {
+
+pxc_status pxc_set_graphs(pxc_workspace* ws, int on) {
+  if (!ws) return fail(PXC_ERR_ARG, "set_graphs: null workspace");
+  WsExtra* x = X(ws);
+  x->graphs = on ? 1 : 0;
+  if (!on) {
+    for (auto& g : x->gcache) cudaGraphExecDestroy(g.exec);
+    x->gcache.clear();
+  }
+  return cuda_check("set_graphs");
+}
+
+pxc_status pxc_graph_stats(pxc_workspace* ws, int64_t* captures, int64_t* replays, int32_t* cached) {
+  if (!ws) return fail(PXC_ERR_ARG, "graph_stats: null workspace");
+  WsExtra* x = X(ws);
+  if (captures) *captures = x->graph_captures;
+  if (replays) *replays = x->graph_hits;
+  if (cached) *cached = (int32_t)x->gcache.size();
+  return PXC_OK;
+}
+
+pxc_status pxc_cross_section(pxc_workspace* ws, const pxc_states* st, const pxc_transitions* tr,
+                             const pxc_condition* c, int32_t n_c, const pxc_grid* grid, const pxc_profile_args* pa,
+                             double threshold, float* sigma_out, int32_t* sigma_exp_out, cudaStream_t s) {
+  if (!ws || !c || n_c < 1 || !sigma_out || !sigma_exp_out || !st || !tr || !grid || !pa)
+    return fail(PXC_ERR_ARG, "cross_section: bad arguments");
+  WsExtra* x = X(ws);
+  if (!x->graphs || ws->accumulate || x->capturing)
+    return cross_section_direct(ws, st, tr, c, n_c, grid, pa, threshold, sigma_out, sigma_exp_out, s);
+  std::vector<unsigned char> key = graph_key(ws, st, tr, c, n_c, grid, pa, threshold, sigma_out, sigma_exp_out, s);
+  for (size_t i = 0; i < x->gcache.size(); ++i) {
+    if (x->gcache[i].key == key) {
+      GraphEntry g = x->gcache[i];
+      x->gcache.erase(x->gcache.begin() + (long)i);
+      x->gcache.push_back(g);
+      ++x->graph_hits;
+      return launch_entry(ws, x->gcache.back(), s);
+    }
+  }
+  // capture the call on the workspace's own stream (the caller's may be the legacy default
+  // stream, which cannot be captured), then launch the instantiated graph on the caller's
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(x->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return cuda_check("cross_section: begin capture");
+  x->capturing = 1;
+  const int64_t before = launches_total();
+  pxc_status r = cross_section_direct(ws, st, tr, c, n_c, grid, pa, threshold, sigma_out, sigma_exp_out,
+                                      x->cap_stream);
+  const int64_t noted = launches_total() - before;
+  note_launches((int)-noted);  // nothing ran yet: the graph's kernels are counted when it launches
+  x->capturing = 0;
+  const cudaError_t ee = cudaStreamEndCapture(x->cap_stream, &graph);
+  if (r) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return r;
+  }
+  if (ee != cudaSuccess || !graph) return fail(PXC_ERR_CUDA, "cross_section: capture failed: %s", cudaGetErrorString(ee));
+  GraphEntry g{};
+  g.key = std::move(key);
+  size_t nn = 0;
+  cudaGraphGetNodes(graph, nullptr, &nn);
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if (nn) cudaGraphGetNodes(graph, nodes.data(), &nn);
+  for (auto& n : nodes) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(n, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++g.kernels;
+  }
+  const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) return fail(PXC_ERR_CUDA, "cross_section: instantiate: %s", cudaGetErrorString(ie));
+  g.last_nseg = x->last_nseg;
+  g.last_seg = x->last_seg;
+  g.last_tile = x->last_tile;
+  g.last_nc = ws->last_nc;
+  if (x->gcache.size() >= kGraphCacheMax) {
+    cudaGraphExecDestroy(x->gcache.front().exec);
+    x->gcache.erase(x->gcache.begin());
+  }
+  x->gcache.push_back(std::move(g));
+  ++x->graph_captures;
+  return launch_entry(ws, x->gcache.back(), s);
 }
 
 pxc_status pxc_cross_section_backward(pxc_workspace* ws, const pxc_states* st, const pxc_transitions* tr,
