@@ -35,14 +35,17 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Voigt line-grid evals/s & lines/s at 1e9 lines; batched, fwd+bwd vs plain"
 UNIT = "line-grid evals/s"
-EVAL_FP32_OPS = 6      # FP32-pipe instructions of one region-I Voigt evaluation (fast path)
-SFU_PER_SM_CLK = 16    # MUFU (rcp/ex2) results per SM per clock; every evaluation needs one
+# Far-wing (W4 region I) evaluation of the profile kernel, per line-grid point:
+#   x = fma(m, step, x0), v = fma(x, x, c1), den = fma(v, v, e), num = fma(v, K, K),
+#   acc = fma(num, rcp(den), acc)
+# five FP32 FMAs (ten FLOPs) and one MUFU reciprocal: the algorithmic work of one evaluation.
+EVAL_FP32_FMAS = 5
+EVAL_MUFU = 1
 L2_BYTES = 126 * 2 ** 20
 
-# DRAM traffic per profile-kernel launch from the committed ncu capture, valid only for
-# the kernel source it was taken on (sha256 prefix of kernels_profile.cu).
-# Both come from an ncu capture of the 2e7-line case, scaled x5 to one 1e8-line launch.
-NCU_TRAFFIC = {("profile", "d0f409663eef7981"): 90473960, ("intensity", "4e40566b8da31649"): 9564512080}
+# DRAM traffic per launch from a committed ncu capture, valid only for the kernel source it was
+# taken on (sha256 prefix of the .cu file); scaled to one 1e8-line launch (see profiles/).
+NCU_TRAFFIC = {}
 
 
 def _src_hash(rel):
@@ -137,26 +140,43 @@ def _cpu_model() -> str:
     return "unknown"
 
 
-def oracle_sample_rate(w, E, g, n_lines, threads):
-    """Oracle throughput (evals/s) on the first n_lines transitions of the workload, full grid."""
+def _conditions(w):
+    """(T, T_vib, P) conditions of a workload: its batched table, else its one condition."""
+    if w.conditions:
+        return [(float(T), 0.0, float(P)) for T, P in w.conditions]
+    return [(w.T, w.T_vib, w.P)]
+
+
+def _oracle_condition(w):
+    """The condition the CPU baseline times: the workload's own, or the table's middle one."""
+    c = _conditions(w)
+    return c[len(c) // 2]
+
+
+def oracle_sample(w, states, n_lines):
+    """The FP64 oracle (Q, intensities, sort, sigma on the full grid) on the first n_lines
+    transitions of the workload at one condition: (evals of non-zero lines, lines, seconds, result)."""
     import numpy as np
     import oracle
+    E, g, Ev = states
+    T, Tv, P = _oracle_condition(w)
     up, lo, A = w.transitions(0, n_lines)
     gr, ne = w.broadening(0, n_lines)
     t0 = time.perf_counter()
-    r = oracle.run(E, g, None, up, lo, A, gr, ne, kind=w.profile, T=w.T, P=w.P, mass_da=w.mass_da,
-                   nu_min=w.nu_min, dnu=w.dnu, n_grid=w.n_grid, cut=w.cutoff, threshold=w.threshold)
+    r = oracle.run(E, g, Ev if Tv > 0 else None, up, lo, A, gr, ne, kind=w.profile, T=T, T_vib=Tv, P=P,
+                   mass_da=w.mass_da, hwhm=w.hwhm, nu_min=w.nu_min, dnu=w.dnu, n_grid=w.n_grid, cut=w.cutoff,
+                   threshold=w.threshold)
     dt = time.perf_counter() - t0
     nz = r["keep"].astype(bool) & (r["I_s"] != 0)
     evals = int(np.sum((r["ihi"] - r["ilo"] + 1)[nz]))
-    return evals, n_lines, dt
+    return evals, n_lines, dt, r
 
 
-def calibrate_sample(w, E, g, threads, target_s):
-    n0 = 200_000
-    ev, n, dt = oracle_sample_rate(w, E, g, n0, threads)
-    n1 = int(min(max(n0 * target_s / max(dt, 1e-3), n0), 5e7))
-    return n1
+def calibrate_sample(w, states, target_s):
+    """Lines of a bounded oracle sample taking about target_s seconds (whole list if smaller)."""
+    n0 = min(200_000, w.n_trans)
+    _, _, dt, _ = oracle_sample(w, states, n0)
+    return int(min(max(n0 * target_s / max(dt, 1e-3), n0), 5e7, w.n_trans))
 
 
 def run_reference(args):
@@ -166,17 +186,18 @@ def run_reference(args):
     import synth
     w = synth.workload(args.workload)
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    E, g, _ = w.states()
-    n = calibrate_sample(w, E, g, threads, args.ref_step_s)
+    states = w.states()
+    n = calibrate_sample(w, states, args.ref_step_s)
     for _ in range(args.warmup):
-        oracle_sample_rate(w, E, g, n, threads)
+        oracle_sample(w, states, n)
     tot_ev, tot_t = 0, 0.0
     for _ in range(args.steps):
-        ev, _, dt = oracle_sample_rate(w, E, g, n, threads)
+        ev, _, dt, _ = oracle_sample(w, states, n)
         tot_ev += ev
         tot_t += dt
     val = tot_ev / tot_t
-    sample = f"first {n} of {w.n_trans} transitions per step, full grid (oracle FP64, {threads} threads)"
+    sample = (f"first {n} of {w.n_trans} transitions per step, full grid, condition {_oracle_condition(w)} "
+              f"(oracle FP64, {threads} threads)")
     out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -186,6 +207,19 @@ def run_reference(args):
            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
     return 0
+
+
+def sigma_errors(got, ref):
+    """Error of a GPU sigma against the oracle's: max |d| over the peak, the worst per-bin relative
+    error where the reference is above 1e-6 of its peak, and the normalised L1 error (Eq. of Sec. 4)."""
+    import numpy as np
+    m = float(np.abs(ref).max())
+    if m == 0.0:
+        return {"max_abs_rel_peak": float(np.abs(got).max()), "worst_bin_rel": None, "l1": None}
+    d = np.abs(got - ref)
+    big = np.abs(ref) > 1e-6 * m
+    return {"max_abs_rel_peak": float(d.max() / m), "worst_bin_rel": float((d[big] / np.abs(ref[big])).max()),
+            "l1": float(d.sum() / np.abs(ref).sum())}
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -203,14 +237,22 @@ def main_pxc(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     pxc.load()
+    pipes = pxc.pxc_pipe_rates()   # measured FP32 / MUFU rates of this GPU (untimed)
 
     w = synth.workload(args.workload)
     if args.lines:
         w = w.scaled(n_trans=args.lines)
+    conds = _conditions(w)
+    n_c = len(conds)
+    batched = n_c > 1
     chunk = w.chunk or w.n_trans
     nchunks = (w.n_trans + chunk - 1) // chunk
-    E, g, _ = w.states()
-    states = pxc.States(torch.from_numpy(E).to(dev), torch.from_numpy(g).to(dev), None)
+    states_h = w.states()
+    E, g, Ev = states_h
+    two_t = any(c[1] > 0 for c in conds)
+    states = pxc.States(torch.from_numpy(E).to(dev), torch.from_numpy(g).to(dev),
+                        torch.from_numpy(Ev).to(dev) if two_t else None)
+    broad = w.profile in ("lorentz", "voigt", "binned_lorentz", "binned_voigt")
 
     # host (pinned) and device copies of the transition list
     a_dtype = torch.float32 if w.A_f32 else torch.float64
@@ -237,52 +279,67 @@ def main_pxc(args):
             d[sl].copy_(h[sl], non_blocking=False)
     t_gen = time.perf_counter() - t_gen
 
-    ws = pxc.Workspace(max_states=w.n_states, max_lines=chunk, max_grid=w.n_grid, device=dev)
+    nT = len({(c[0], c[1]) for c in conds})
+    ws = pxc.Workspace(max_states=w.n_states, max_lines=chunk, max_grid=w.n_grid, max_conditions=n_c,
+                       max_temperatures=nT, device=dev)
     grid = (w.nu_min, w.dnu, w.n_grid)
-    cond = (w.T, w.T_vib, w.P)
-    sigma = torch.empty(w.n_grid, dtype=torch.float32, device=dev)
-    sexp = torch.empty(1, dtype=torch.int32, device=dev)
+    sigma = torch.empty(n_c, w.n_grid, dtype=torch.float32, device=dev)
+    sexp = torch.empty(n_c, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
+    cond_arg = conds if batched else conds[0]
 
-    def step():
-        ws.set_accumulate(True)
-        sigma.zero_()
-        sexp.fill_(pxc.PXC_EXP_EMPTY)
+    def chunk_args(c):
+        t0, n = c * chunk, min(chunk, w.n_trans - c * chunk)
+        sl = slice(t0, t0 + n)
+        tr = pxc.Transitions(d_up[sl], d_lo[sl], d_A[sl])
+        prof = pxc.Profile(w.profile, w.cutoff, w.mass_da, w.hwhm, d_gr[sl] if broad else None,
+                           d_ne[sl] if broad else None)
+        return tr, prof
+
+    def step(count=None):
+        ws.set_accumulate(nchunks > 1)
+        if nchunks > 1:
+            sigma.zero_()
+            sexp.fill_(pxc.PXC_EXP_EMPTY)
         for c in range(nchunks):
-            t0, n = c * chunk, min(chunk, w.n_trans - c * chunk)
-            sl = slice(t0, t0 + n)
-            tr = pxc.Transitions(d_up[sl], d_lo[sl], d_A[sl])
-            prof = pxc.Profile(w.profile, w.cutoff, w.mass_da, w.hwhm, d_gr[sl], d_ne[sl])
-            pxc.pxc_cross_section(ws, states, tr, cond, grid, prof, w.threshold, sigma=sigma.view(1, -1),
-                                  sigma_exp=sexp)
+            tr, prof = chunk_args(c)
+            pxc.pxc_cross_section(ws, states, tr, cond_arg, grid, prof, w.threshold, sigma=sigma, sigma_exp=sexp)
+            if count is not None:
+                s = ws.stats()
+                for k in count:
+                    count[k] += s[{"evals": "evals_nonzero", "evals_window": "evals_window",
+                                   "kept": "n_kept"}[k]]
         ws.set_accumulate(False)
 
     # tile configuration of the profile kernel: timed on the first chunk (setup, untimed)
     tune = None
+    kind_id = pxc.PROFILES[w.profile]
     if args.tile < 0:
-        n0 = min(chunk, w.n_trans)
-        tr0 = pxc.Transitions(d_up[:n0], d_lo[:n0], d_A[:n0])
-        pr0 = pxc.Profile(w.profile, w.cutoff, w.mass_da, w.hwhm, d_gr[:n0], d_ne[:n0])
-        t_best, t_ms, _, _ = pxc.pxc_autotune(ws, states, tr0, cond, grid, pr0, w.threshold, repeats=2,
-                                              sigma=sigma.view(1, -1), sigma_exp=sexp)
+        tr0, pr0 = chunk_args(0)
+        t_best, t_ms, _, _ = pxc.pxc_autotune(ws, states, tr0, cond_arg, grid, pr0, w.threshold, repeats=2,
+                                              sigma=sigma, sigma_exp=sexp)
         tune = {"tile": t_best, "ms_per_chunk_call": t_ms}
     else:
-        ws.set_tile(pxc.PROFILES[w.profile], False, args.tile)
-    tile = ws.get_tile(pxc.PROFILES[w.profile], False)
+        ws.set_tile(kind_id, batched, args.tile)
+    tile = ws.get_tile(kind_id, batched)
 
-    # one counted step: algorithmic eval counts per chunk
-    ws.set_accumulate(True)
-    sigma.zero_(); sexp.fill_(pxc.PXC_EXP_EMPTY)
-    evals = evals_window = kept = 0
-    for c in range(nchunks):
-        t0, n = c * chunk, min(chunk, w.n_trans - c * chunk)
-        sl = slice(t0, t0 + n)
-        tr = pxc.Transitions(d_up[sl], d_lo[sl], d_A[sl])
-        prof = pxc.Profile(w.profile, w.cutoff, w.mass_da, w.hwhm, d_gr[sl], d_ne[sl])
-        pxc.pxc_cross_section(ws, states, tr, cond, grid, prof, w.threshold, sigma=sigma.view(1, -1), sigma_exp=sexp)
-        s = ws.stats()
-        evals += s["evals_nonzero"]; evals_window += s["evals_window"]; kept += s["n_kept"]
-    ws.set_accumulate(False)
+    # one counted step: algorithmic eval counts (the stats cover the last condition of a batched
+    # call, so a table counts each condition's evaluations from one call per condition)
+    count = {"evals": 0, "evals_window": 0, "kept": 0}
+    if batched:
+        wsc = pxc.Workspace(max_states=w.n_states, max_lines=chunk, max_grid=w.n_grid, device=dev)
+        s1 = torch.empty(1, w.n_grid, dtype=torch.float32, device=dev)
+        e1 = torch.empty(1, dtype=torch.int32, device=dev)
+        tr0, pr0 = chunk_args(0)
+        for cnd in conds:
+            pxc.pxc_cross_section(wsc, states, tr0, cnd, grid, pr0, w.threshold, sigma=s1, sigma_exp=e1)
+            st_ = wsc.stats()
+            count["evals"] += st_["evals_nonzero"]; count["evals_window"] += st_["evals_window"]
+            count["kept"] += st_["n_kept"]
+        del wsc, s1, e1
+    else:
+        step(count)
+    evals, evals_window, kept = count["evals"], count["evals_window"], count["kept"]
     ws.sync()
 
     for _ in range(args.warmup):
@@ -315,83 +372,111 @@ def main_pxc(args):
     value = replica_rate(evals, args.steps, world, ms_max)
     lines_per_s = replica_rate(w.n_trans, args.steps, world, ms_max)
 
-    # ---------------------------------------------------------------- e2e through the host-streaming ABI call
+    # ---------------------------------------------------------------- e2e through the public API, host buffers
     e2e = None
     if not args.no_e2e:
-        bufs = None
-        h_sig = torch.empty(w.n_grid, dtype=torch.float32, pin_memory=True)
-        h_exp = torch.empty(1, dtype=torch.int32, pin_memory=True)
-        prof0 = pxc.Profile(w.profile, w.cutoff, w.mass_da, w.hwhm, None, None)
+        h_sig = torch.empty(n_c, w.n_grid, dtype=torch.float32, pin_memory=True)
+        h_exp = torch.empty(n_c, dtype=torch.int32, pin_memory=True)
+        asz = 4 if w.A_f32 else 8
+        h2d = w.n_trans * (4 + 4 + asz + (8 if broad else 0))
+        if not batched:
+            bufs = None
+            prof0 = pxc.Profile(w.profile, w.cutoff, w.mass_da, w.hwhm, None, None)
+            s1, e1 = sigma[0], sexp[0:1]
 
-        def step_e2e(bufs):
-            sig, e, bufs = pxc.pxc_cross_section_streamed(ws, states, h_up, h_lo, h_A, h_gr, h_ne, cond, grid, prof0,
-                                                          w.threshold, bufs=bufs, sigma=sigma, sigma_exp=sexp)
-            h_sig.copy_(sig, non_blocking=True)
-            h_exp.copy_(e, non_blocking=True)
-            return bufs
+            def step_e2e(bufs):
+                sig, e, bufs = pxc.pxc_cross_section_streamed(ws, states, h_up, h_lo, h_A, h_gr if broad else None,
+                                                              h_ne if broad else None, cond_arg, grid, prof0,
+                                                              w.threshold, bufs=bufs, sigma=s1, sigma_exp=e1)
+                h_sig[0].copy_(sig, non_blocking=True)
+                h_exp.copy_(e, non_blocking=True)
+                return bufs
+        else:
+            def step_e2e(bufs):
+                for d, h in ((d_up, h_up), (d_lo, h_lo), (d_A, h_A), (d_gr, h_gr), (d_ne, h_ne)):
+                    d.copy_(h, non_blocking=True)
+                tr, prof = chunk_args(0)
+                pxc.pxc_cross_section(ws, states, tr, cond_arg, grid, prof, w.threshold, sigma=sigma,
+                                      sigma_exp=sexp)
+                h_sig.copy_(sigma, non_blocking=True)
+                h_exp.copy_(sexp, non_blocking=True)
+                return bufs
 
-        bufs = step_e2e(bufs)
+        bufs = step_e2e(None)
         ws.sync()
-        n_e2e = max(1, min(args.steps, 3))
+        n_e2e = args.steps
         barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0, e1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(n_e2e):
             bufs = step_e2e(bufs)
-        e1.record(stream)
+        e1_.record(stream)
         barrier()
-        ms_e = e0.elapsed_time(e1)
-        ms_e = slowest_rank_ms(ms_e, world, dev)
-        h2d = w.n_trans * (4 + 4 + (4 if w.A_f32 else 8) + 8)
+        ms_e = slowest_rank_ms(e0.elapsed_time(e1_), world, dev)
+        d2h = n_c * (w.n_grid * 4 + 4)
         e2e = {"value": replica_rate(evals, n_e2e, world, ms_e), "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": w.n_grid * 4 + 4, "steps": n_e2e, "ms_per_step": ms_e / n_e2e,
-               "lines_per_s": replica_rate(w.n_trans, n_e2e, world, ms_e)}
+               "d2h_bytes_per_step": d2h, "steps": n_e2e, "ms_per_step": ms_e / n_e2e,
+               "lines_per_s": replica_rate(w.n_trans, n_e2e, world, ms_e),
+               "h2d_gbs": h2d / (ms_e / n_e2e / 1e3) / 1e9,
+               "bound": ("host-to-device copy (PCIe): the copies of step c+1 overlap the kernels of step c"
+                         if ms_e / n_e2e > 1.5 * ms_max / args.steps else "kernels")}
 
     # ---------------------------------------------------------------- rooflines
     peaks, peak_src = _peaks()
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     sm_max = float(clk.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2032.0))
-    alu_peak = sms * 128 * sm_max * 1e6 / 1e12            # T FP32 lane-ops/s
-    sfu_peak = sms * SFU_PER_SM_CLK * sm_max * 1e6 / 1e9   # G evaluations/s (one MUFU op each)
+    clk_hz = sm_max * 1e6
+    per_clk = pipes["per_sm_per_clk"]
+    fp32_peak = sms * 128 * 2 * clk_hz / 1e12                 # TFLOP/s: SMs x 128 FMA lanes x 2 x clock
+    fp32_meas = sms * per_clk["fma"] * 2 * clk_hz / 1e12      # the same from the measured FMA rate
+    mufu_peak = sms * per_clk["rcp"] * clk_hz / 1e9           # G reciprocals/s, measured rate
     prof_ms, prof_n = tm["profile"]
     int_ms, int_n = tm["intensity"]
     sort_ms, sort_n = tm["sort"]
-    per_launch_evals = evals / nchunks
+    per_launch_evals = evals / max(prof_n // max(args.steps, 1), 1)
     prof_launch_ms = prof_ms / max(prof_n, 1)
-    ach_evals = per_launch_evals / (prof_launch_ms / 1e3) / 1e9
-    ach_alu = EVAL_FP32_OPS * per_launch_evals / (prof_launch_ms / 1e3) / 1e12
+    ach_evals = per_launch_evals / (prof_launch_ms / 1e3)
+    ach_tflops = 2 * EVAL_FP32_FMAS * ach_evals / 1e12
+    roof_profile = {"bound": "alu", "achieved": ach_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": ach_tflops / fp32_peak, "traffic": NCU_TRAFFIC.get(
+                        ("profile", _src_hash("paper_2609_17273_b300/csrc/kernels_profile.cu"))),
+                    "kernel": f"k_profile<{w.profile}>",
+                    "peak_source": (f"FP32 pipe: {sms} SMs x 128 FMA lanes x 2 FLOP x {sm_max:.0f} MHz "
+                                    f"(measured FMA rate {per_clk['fma']:.1f}/SM/clk: {fp32_meas:.2f} TFLOP/s)"),
+                    "algorithmic": f"{EVAL_FP32_FMAS} FP32 FMAs + {EVAL_MUFU} MUFU rcp per line-grid evaluation",
+                    "evals_per_s": ach_evals,
+                    "mufu": {"achieved_G": ach_evals * EVAL_MUFU / 1e9, "peak_G": mufu_peak,
+                             "frac": ach_evals * EVAL_MUFU / 1e9 / mufu_peak,
+                             "peak_source": f"measured rcp rate {per_clk['rcp']:.2f}/SM/clk"},
+                    "issue": {"frac": ach_evals * (EVAL_FP32_FMAS + EVAL_MUFU) / (sms * 128 * clk_hz),
+                              "note": "warp-instruction issue slots of the algorithmic work (one per SMSP per clock)"},
+                    "launch_ms": prof_launch_ms, "launches_per_step": prof_n / max(args.steps, 1)}
     # algorithmic bytes of one intensity launch: the line arrays read once (upper, lower, A),
     # (key, index, FP64 I) written per kept line, and the 2-byte state-code table read once
     kept_per_launch = kept / nchunks
-    per_launch_bytes = chunk * (4 + 4 + (4 if w.A_f32 else 8)) + kept_per_launch * (8 + 4 + 8) + w.n_states * 2
+    a_bytes = 4 if w.A_f32 else 8
+    per_launch_bytes = chunk * (4 + 4 + a_bytes) + kept_per_launch * (8 + 4 + 8) + w.n_states * 2
     int_launch_ms = int_ms / max(int_n, 1)
-    ach_hbm = per_launch_bytes / (int_launch_ms / 1e3) / 1e9
-    kvh = _src_hash("paper_2609_17273_b300/csrc/kernels_profile.cu")
-    klh = _src_hash("paper_2609_17273_b300/csrc/kernels_lines.cu")
-    tr_prof = NCU_TRAFFIC.get(("profile", kvh))
-    tr_int = NCU_TRAFFIC.get(("intensity", klh))
-    roof_profile = {"bound": "alu", "achieved": ach_evals, "peak": sfu_peak, "unit": "G evals/s",
-                    "frac": ach_evals / sfu_peak, "traffic": tr_prof, "kernel": "k_profile<VOIGT>",
-                    "peak_source": f"{sms} SMs x {SFU_PER_SM_CLK} MUFU results/clk x {sm_max:.0f} MHz "
-                                   "(one rcp per region-I evaluation)",
-                    "fp32_lane_ops": {"achieved_T": ach_alu, "peak_T": alu_peak, "frac": ach_alu / alu_peak,
-                                      "ops_per_eval": EVAL_FP32_OPS},
-                    "launch_ms": prof_launch_ms}
+    ach_hbm = per_launch_bytes / (int_launch_ms / 1e3) / 1e9 if int_n else 0.0
     roof_int = {"bound": "hbm", "achieved": ach_hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach_hbm / peaks["hbm_gbs"], "traffic": tr_int, "kernel": "k_lines_c",
-                "peak_source": f"hbm_gbs of {peak_src}", "bytes_per_line": per_launch_bytes / chunk,
-                "sector_bytes_per_line": 4 + 4 + (4 if w.A_f32 else 8) + 2 * 32,
-                "launch_ms": int_launch_ms}
+                "frac": ach_hbm / peaks["hbm_gbs"], "traffic": NCU_TRAFFIC.get(
+                    ("intensity", _src_hash("paper_2609_17273_b300/csrc/kernels_lines.cu"))),
+                "kernel": "k_lines_c", "peak_source": f"hbm_gbs of {peak_src} MEASURED_PEAKS.json",
+                "bytes_per_line": per_launch_bytes / chunk,
+                "sector_bytes_per_line": 4 + 4 + a_bytes + 2 * 32, "launch_ms": int_launch_ms}
     dominant = roof_profile if prof_ms >= int_ms else roof_int
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": w.name, "lines": w.n_trans, "states": w.n_states, "grid": w.n_grid,
-                      "chunk": chunk, "profile": w.profile, "T": w.T, "P": w.P, "cutoff": w.cutoff,
-                      "threshold": w.threshold, "parallelism": f"replicas x{world}",
-                      "l2": "inputs (20 GB) larger than L2", "fp64": "nu, Boltzmann factors, Q",
+                      "chunk": chunk, "conditions": n_c, "profile": w.profile, "T": w.T, "T_vib": w.T_vib,
+                      "P": w.P, "cutoff": w.cutoff, "threshold": w.threshold,
+                      "parallelism": f"replicas x{world}",
+                      "l2": f"inputs ({w.n_trans * (16 if w.A_f32 else 20) / 1e9:.1f} GB) larger than L2"
+                            if w.n_trans * 16 > L2_BYTES else "inputs smaller than L2",
+                      "fp64": "nu, Boltzmann factors, Q",
                       "profile_tile": {"tile": tile, "segment_points": pxc.TILE_SEGMENT_POINTS[tile],
                                        "autotune": tune}},
            "lines_per_s": lines_per_s,
@@ -399,21 +484,32 @@ def main_pxc(args):
            "pass_ms_per_step": {"intensity": int_ms / args.steps, "sort": sort_ms / args.steps,
                                 "profile": prof_ms / args.steps},
            "roofline": dominant, "rooflines": {"profile": roof_profile, "intensity": roof_int},
-           "gpu_launches": launches, "clocks": clk, "e2e": e2e, "setup_s": t_gen}
+           "pipe_rates": pipes, "gpu_launches": launches, "clocks": clk, "e2e": e2e, "setup_s": t_gen}
 
     if rank == 0 and not args.no_extras:
         out["extras"] = run_extras(args, pxc, torch, dev, synth)
     if rank == 0 and not args.no_cpu_baseline:
         threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-        n = calibrate_sample(w, E, g, threads, args.ref_step_s)
-        ev, nl, dt = oracle_sample_rate(w, E, g, n, threads)
+        n = calibrate_sample(w, states_h, args.ref_step_s)
+        ev, nl, dt, r = oracle_sample(w, states_h, n)
+        # the GPU on the same sample and condition: its error against the oracle
+        wsx = pxc.Workspace(max_states=w.n_states, max_lines=nl, max_grid=w.n_grid, device=dev)
+        trx = pxc.Transitions(d_up[:nl], d_lo[:nl], d_A[:nl])
+        prx = pxc.Profile(w.profile, w.cutoff, w.mass_da, w.hwhm, d_gr[:nl] if broad else None,
+                          d_ne[:nl] if broad else None)
+        sx, ex = pxc.pxc_cross_section(wsx, states, trx, _oracle_condition(w), grid, prx, w.threshold)
+        wsx.sync()
+        got = np.ldexp(sx[0].double().cpu().numpy(), int(ex[0].item()))
+        del wsx
         out["cpu_baseline"] = {"value": ev / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-                               "sample": f"first {nl} of {w.n_trans} transitions, full grid, {dt:.1f} s",
-                               "cpu": _cpu_model()}
+                               "sample": (f"first {nl} of {w.n_trans} transitions, full grid, condition "
+                                          f"{_oracle_condition(w)}, {dt:.1f} s"),
+                               "cpu": _cpu_model(), "oracle_s": dt,
+                               "gpu_error_vs_oracle": sigma_errors(got, r["sigma"])}
         # the same oracle on one thread, on a sample a `threads`-th the size
         import oracle
         oracle.set_threads(1)
-        ev1, nl1, dt1 = oracle_sample_rate(w, E, g, max(1000, n // max(threads, 1)), 1)
+        ev1, nl1, dt1, _ = oracle_sample(w, states_h, max(1000, n // max(threads, 1)))
         oracle.set_threads(threads)
         out["cpu_baseline"]["one_thread"] = {"value": ev1 / dt1, "sample": f"first {nl1} transitions, {dt1:.1f} s"}
     if rank == 0:

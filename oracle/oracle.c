@@ -610,18 +610,29 @@ int orc_cross_section(int kind, const double* nu, const double* I, const double*
   return ORC_OK;
 }
 
-/* The same sum on the grid points i0 .. i0+m-1 only (sampled checks at full size). */
+/* The same sum on the grid points i0 .. i0+m-1 only (sampled checks at full size).  As in
+ * orc_cross_section, the points are split among threads and each point sums its lines in
+ * transition-index order. */
 int orc_cross_section_window(int kind, const double* nu, const double* I, const double* alpha, const double* gamma,
                              const uint8_t* keep, const int64_t* ilo, const int64_t* ihi, int64_t n,
                              double nu_min, double dnu, int64_t i0, int64_t m, double* sigma) {
   if (!gl_ready) gl_init();
   for (int64_t j = 0; j < m; ++j) sigma[j] = 0.0;
-  for (int64_t t = 0; t < n; ++t) {
-    if (!keep[t] || ihi[t] < i0 || ilo[t] > i0 + m - 1) continue;
-    int64_t lo = ilo[t] > i0 ? ilo[t] : i0, hi = ihi[t] < i0 + m - 1 ? ihi[t] : i0 + m - 1;
-    for (int64_t i = lo; i <= hi; ++i) {
-      double x = (nu_min + (double)i * dnu) - nu[t];
-      sigma[i - i0] += I[t] * prof_point(kind, x, dnu, alpha[t], gamma[t]);
+  int64_t nblk = m < 64 ? m : 64;
+  if (nblk < 1) return ORC_OK;
+  int64_t bs = (m + nblk - 1) / nblk;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t b = 0; b < nblk; ++b) {
+    int64_t a0 = i0 + b * bs, a1 = a0 + bs - 1;
+    if (a1 > i0 + m - 1) a1 = i0 + m - 1;
+    if (a0 > a1) continue;
+    for (int64_t t = 0; t < n; ++t) {
+      if (!keep[t] || ihi[t] < a0 || ilo[t] > a1) continue;
+      int64_t lo = ilo[t] > a0 ? ilo[t] : a0, hi = ihi[t] < a1 ? ihi[t] : a1;
+      for (int64_t i = lo; i <= hi; ++i) {
+        double x = (nu_min + (double)i * dnu) - nu[t];
+        sigma[i - i0] += I[t] * prof_point(kind, x, dnu, alpha[t], gamma[t]);
+      }
     }
   }
   return ORC_OK;
