@@ -24,7 +24,8 @@ _LIB = os.path.join(_HERE, "_oracle.so")
 _lib = None
 
 KIND = {"gauss_doppler": 0, "gauss_hwhm": 1, "lorentz": 2, "voigt": 3,
-        "binned_gauss_doppler": 4, "binned_gauss_hwhm": 5, "binned_lorentz": 6, "binned_voigt": 7}
+        "binned_gauss_doppler": 4, "binned_gauss_hwhm": 5, "binned_lorentz": 6, "binned_voigt": 7,
+        "pv_thompson": 8, "pv_olivero": 9, "pv_liulin": 10}
 STATUS = {0: "ok", 1: "bad argument", 2: "state id out of range", 3: "non-finite input",
           4: "Boltzmann exponent overflow"}
 
@@ -51,6 +52,7 @@ def _load():
         L.orc_profile.argtypes = [cint, i64, P, dbl, dbl, P, P, P]
         L.orc_partition.argtypes = [P, P, P, i64, dbl, dbl, P]
         L.orc_profile_binned.argtypes = [cint, i64, P, dbl, dbl, dbl, P]
+        L.orc_pv_params.argtypes = [cint, i64, P, P, P, P, P]
         L.orc_line_intensities.argtypes = [P, P, P, i64, P, P, P, cint, i64, dbl, dbl, dbl,
                                            dbl, dbl, i64, dbl, dbl, P, P, P, P, P]
         L.orc_partition_density.argtypes = [P, P, P, P, i64, dbl, P]
@@ -124,6 +126,15 @@ def profile_binned(kind: str, x, dnu: float, alpha: float, gamma: float = 0.0):
     f = np.empty_like(x)
     _load().orc_profile_binned(KIND[kind.replace("binned_", "")], x.size, _p(x), dnu, alpha, gamma, _p(f))
     return f
+
+
+def pv_params(kind: str, alpha, gamma):
+    """(G, w_L, w_G) of a pseudo-Voigt kind: the common full width and the weights of its
+    Lorentzian and Gaussian, from Doppler and Lorentz HWHMs (reading R20 in oracle.c)."""
+    a = _c(np.atleast_1d(alpha), np.float64); g = _c(np.broadcast_to(gamma, a.shape), np.float64)
+    G = np.empty_like(a); wl = np.empty_like(a); wg = np.empty_like(a)
+    _load().orc_pv_params(KIND[kind], a.size, _p(a), _p(g), _p(G), _p(wl), _p(wg))
+    return G, wl, wg
 
 
 def partition(E, g, E_vib=None, T=296.0, T_vib=0.0):
