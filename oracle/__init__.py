@@ -54,20 +54,20 @@ def _load():
         L.orc_profile_binned.argtypes = [cint, i64, P, dbl, dbl, dbl, P]
         L.orc_pv_params.argtypes = [cint, i64, P, P, P, P, P]
         L.orc_line_intensities.argtypes = [P, P, P, i64, P, P, P, cint, i64, dbl, dbl, dbl,
-                                           dbl, dbl, i64, dbl, dbl, P, P, P, P, P]
+                                           dbl, dbl, i64, dbl, dbl, dbl, P, P, P, P, P]
         L.orc_partition_density.argtypes = [P, P, P, P, i64, dbl, P]
         L.orc_intensities.argtypes = [cint, P, P, P, P, i64, P, P, P, cint, i64, dbl, dbl, dbl,
-                                      dbl, dbl, i64, dbl, dbl, P, P, P, P, P]
+                                      dbl, dbl, i64, dbl, dbl, dbl, P, P, P, P, P]
         L.orc_cooling_function.argtypes = [P, P, P, P, i64, P, P, P, cint, i64, dbl, dbl, dbl, P]
         L.orc_list_exponent.argtypes = [P, P, i64]
         L.orc_list_exponent.restype = ctypes.c_int32
         L.orc_scale_intensities.argtypes = [P, P, i64, ctypes.c_int32, P]
-        L.orc_sorted_order.argtypes = [P, P, i64, P]
+        L.orc_sorted_order.argtypes = [P, P, i64, dbl, P]
         L.orc_sorted_order.restype = i64
         L.orc_segment_ranges.argtypes = [P, P, i64, i64, i64, P, P]
         L.orc_widths.argtypes = [cint, P, P, P, i64, dbl, dbl, dbl, dbl, dbl, P, P]
-        L.orc_cross_section.argtypes = [cint, P, P, P, P, P, P, P, i64, dbl, dbl, i64, P]
-        L.orc_cross_section_window.argtypes = [cint, P, P, P, P, P, P, P, i64, dbl, dbl, i64, i64, P]
+        L.orc_cross_section.argtypes = [cint, P, P, P, P, P, P, P, i64, dbl, dbl, i64, dbl, P]
+        L.orc_cross_section_window.argtypes = [cint, P, P, P, P, P, P, P, i64, dbl, dbl, i64, i64, dbl, P]
         L.orc_cross_section_grad.argtypes = [cint, P, P, P, P, P, cint, P, P, P, P, P, P, P, P, i64,
                                              dbl, dbl, dbl, dbl, P, dbl, dbl, P, P, P, P, P, P]
         _lib = L
@@ -145,8 +145,10 @@ def partition(E, g, E_vib=None, T=296.0, T_vib=0.0):
     return out
 
 
-def line_intensities(E, g, E_vib, upper, lower, A, T, T_vib, Q, nu_min, dnu, n_grid, cut, threshold=0.0):
-    """Per-transition nu, I (cm/molecule, 0 where dropped), keep, ilo, ihi."""
+def line_intensities(E, g, E_vib, upper, lower, A, T, T_vib, Q, nu_min, dnu, n_grid, cut, threshold=0.0,
+                     wl_unit=0.0):
+    """Per-transition nu, I (cm/molecule, 0 where dropped), keep, ilo, ihi.  wl_unit > 0 makes the
+    grid (nu_min, dnu) a wavelength grid in that unit (1e7: nm, 1e4: um; reading R21)."""
     E = _c(E, np.float64); g = _c(g, np.int32); Ev = _c(E_vib, np.float64)
     up = _c(upper, np.int32); lo = _c(lower, np.int32)
     A_f32 = A.dtype == np.float32
@@ -155,7 +157,7 @@ def line_intensities(E, g, E_vib, upper, lower, A, T, T_vib, Q, nu_min, dnu, n_g
     nu = np.empty(n); I = np.empty(n); keep = np.empty(n, np.uint8)
     ilo = np.empty(n, np.int64); ihi = np.empty(n, np.int64)
     _chk(_load().orc_line_intensities(_p(E), _p(g), _p(Ev), E.size, _p(up), _p(lo), _p(A), int(A_f32), n,
-                                      T, T_vib, Q, nu_min, dnu, n_grid, cut, threshold,
+                                      T, T_vib, Q, nu_min, dnu, n_grid, cut, threshold, wl_unit,
                                       _p(nu), _p(I), _p(keep), _p(ilo), _p(ihi)))
     return nu, I, keep, ilo, ihi
 
@@ -169,7 +171,7 @@ def partition_density(E, g, E_vib, n_vib, T_rot):
 
 
 def intensities(E, g, E_vib, upper, lower, A, T, T_vib, Q, nu_min, dnu, n_grid, cut, threshold=0.0,
-                emission=False, n_vib=None):
+                emission=False, n_vib=None, wl_unit=0.0):
     """Per-transition nu, value (absorption cm/molecule or emission erg/s/sr/molecule), keep, ilo, ihi
     for the LTE, two-temperature (T_vib > 0) or vibronic-density (n_vib given) populations."""
     E = _c(E, np.float64); g = _c(g, np.int32); Ev = _c(E_vib, np.float64); nv = _c(n_vib, np.float64)
@@ -180,7 +182,7 @@ def intensities(E, g, E_vib, upper, lower, A, T, T_vib, Q, nu_min, dnu, n_grid, 
     nu = np.empty(n); I = np.empty(n); keep = np.empty(n, np.uint8)
     ilo = np.empty(n, np.int64); ihi = np.empty(n, np.int64)
     _chk(_load().orc_intensities(int(bool(emission)), _p(E), _p(g), _p(Ev), _p(nv), E.size, _p(up), _p(lo), _p(A),
-                                 int(A_f32), n, T, T_vib, Q, nu_min, dnu, n_grid, cut, threshold,
+                                 int(A_f32), n, T, T_vib, Q, nu_min, dnu, n_grid, cut, threshold, wl_unit,
                                  _p(nu), _p(I), _p(keep), _p(ilo), _p(ihi)))
     return nu, I, keep, ilo, ihi
 
@@ -209,11 +211,12 @@ def scale_intensities(I, keep, k):
     return out
 
 
-def sorted_order(nu, keep):
-    """Kept transition indices in ascending (nu bits, index) order."""
+def sorted_order(nu, keep, wl_unit=0.0):
+    """Kept transition indices in ascending (nu bits, index) order (descending nu bits on a
+    wavelength grid)."""
     nu = _c(nu, np.float64); keep = _c(keep, np.uint8)
     perm = np.empty(nu.size, np.int64)
-    m = _load().orc_sorted_order(_p(nu), _p(keep), nu.size, _p(perm))
+    m = _load().orc_sorted_order(_p(nu), _p(keep), nu.size, wl_unit, _p(perm))
     return perm[:m].copy()
 
 
@@ -234,25 +237,25 @@ def widths(kind, nu, gamma_ref, n_T, T, P, mass_da=18.0, hwhm=0.0, T_ref=296.0):
     return a, gm
 
 
-def cross_section(kind, nu, I, alpha, gamma, keep, ilo, ihi, nu_min, dnu, n_grid):
+def cross_section(kind, nu, I, alpha, gamma, keep, ilo, ihi, nu_min, dnu, n_grid, wl_unit=0.0):
     """sigma on the grid (cm^2/molecule), Eq. (xsec)."""
     nu = _c(np.where(keep.astype(bool), nu, 0.0), np.float64)
     I = _c(I, np.float64); alpha = _c(alpha, np.float64); gamma = _c(gamma, np.float64)
     keep = _c(keep, np.uint8); ilo = _c(ilo, np.int64); ihi = _c(ihi, np.int64)
     sig = np.empty(n_grid)
     _chk(_load().orc_cross_section(KIND[kind], _p(nu), _p(I), _p(alpha), _p(gamma), _p(keep), _p(ilo), _p(ihi),
-                                   nu.size, nu_min, dnu, n_grid, _p(sig)))
+                                   nu.size, nu_min, dnu, n_grid, wl_unit, _p(sig)))
     return sig
 
 
-def cross_section_window(kind, nu, I, alpha, gamma, keep, ilo, ihi, nu_min, dnu, i0, m):
+def cross_section_window(kind, nu, I, alpha, gamma, keep, ilo, ihi, nu_min, dnu, i0, m, wl_unit=0.0):
     """sigma at grid indices i0 .. i0+m-1 only (same grid points as the full grid)."""
     nu = _c(np.where(keep.astype(bool), nu, 0.0), np.float64)
     I = _c(I, np.float64); alpha = _c(alpha, np.float64); gamma = _c(gamma, np.float64)
     keep = _c(keep, np.uint8); ilo = _c(ilo, np.int64); ihi = _c(ihi, np.int64)
     sig = np.empty(m)
     _chk(_load().orc_cross_section_window(KIND[kind], _p(nu), _p(I), _p(alpha), _p(gamma), _p(keep), _p(ilo),
-                                          _p(ihi), nu.size, nu_min, dnu, i0, m, _p(sig)))
+                                          _p(ihi), nu.size, nu_min, dnu, i0, m, wl_unit, _p(sig)))
     return sig
 
 
@@ -281,7 +284,7 @@ def cross_section_grad(kind, E, E_vib, upper, lower, A, nu, I, alpha, gamma, n_T
 
 def run(E, g, E_vib, upper, lower, A, gamma_ref, n_T, *, kind, T, T_vib=0.0, P=1.0, mass_da=18.0,
         hwhm=0.0, nu_min, dnu, n_grid, cut, threshold=0.0, T_ref=296.0, with_sigma=True,
-        emission=False, n_vib=None):
+        emission=False, n_vib=None, wl_unit=0.0):
     """Whole forward path: Q, per-line quantities, exponent, sort order, sigma (absorption or
     emission; LTE, two-temperature or vibronic-density populations)."""
     if n_vib is not None:
@@ -290,18 +293,18 @@ def run(E, g, E_vib, upper, lower, A, gamma_ref, n_T, *, kind, T, T_vib=0.0, P=1
         Qd = partition(E, g, E_vib if T_vib > 0 else None, T, T_vib)
     if emission or n_vib is not None:
         nu, I, keep, ilo, ihi = intensities(E, g, E_vib, upper, lower, A, T, T_vib, Qd[0], nu_min, dnu, n_grid,
-                                            cut, threshold, emission=emission, n_vib=n_vib)
+                                            cut, threshold, emission=emission, n_vib=n_vib, wl_unit=wl_unit)
     else:
         nu, I, keep, ilo, ihi = line_intensities(E, g, E_vib, upper, lower, A, T, T_vib, Qd[0],
-                                                 nu_min, dnu, n_grid, cut, threshold)
+                                                 nu_min, dnu, n_grid, cut, threshold, wl_unit=wl_unit)
     k = list_exponent(I, keep)
     I_s = scale_intensities(I, keep, k)
-    perm = sorted_order(nu, keep)
+    perm = sorted_order(nu, keep, wl_unit)
     nu_w = np.where(keep.astype(bool), nu, 1.0)
     alpha, gamma = widths(kind, nu_w, gamma_ref, n_T, T, P, mass_da, hwhm, T_ref)
     out = {"Q": Qd, "nu": nu, "I": I, "keep": keep, "ilo": ilo, "ihi": ihi, "k": k, "I_s": I_s,
            "perm": perm, "alpha": alpha, "gamma": gamma,
            "evals": int(np.sum((ihi - ilo + 1)[keep.astype(bool)]))}
     if with_sigma:
-        out["sigma"] = cross_section(kind, nu, I, alpha, gamma, keep, ilo, ihi, nu_min, dnu, n_grid)
+        out["sigma"] = cross_section(kind, nu, I, alpha, gamma, keep, ilo, ihi, nu_min, dnu, n_grid, wl_unit)
     return out

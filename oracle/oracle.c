@@ -56,6 +56,14 @@
  *           - 0.18384 d^2 - 0.11568 d^3, c_G = 0.32460 - 0.61825 d + 0.17681 d^2 + 0.12109 d^3.
  *       The Kielkopf and Di Rocco-Cruzado variants the table also names are not written: their
  *       coefficients are in publications this restatement could not consult.
+ *   R21 wavelength grids (Sec. 2.4.3: spectra in wavenumber, or in wavelength in nm or um): a
+ *       grid uniform in wavelength, lambda_i = lambda_min + i dlambda in a unit with
+ *       nu = U / lambda (U = 1e7 for nm, 1e4 for um); sigma is sampled at nu_i = U / lambda_i and
+ *       the cut-off stays in cm^-1.  |nu_i - nu_l| <= cut is U/(nu_l + cut) <= lambda_i <=
+ *       U/(nu_l - cut), so the window is i_lo = ceil((U/(nu + cut) - lambda_min)/dlambda),
+ *       i_hi = floor((U/(nu - cut) - lambda_min)/dlambda) (the last point when nu <= cut), plain
+ *       IEEE double, clamped; lines are ordered by descending nu (ascending wavelength), ties by
+ *       transition index, so windows stay monotone along the order.  Sampled profiles only.
  *   R18 vibronic densities: E_rot = E - E_vib within each manifold, T (the condition's
  *       temperature) is T_rot, and the densities are used as given (every formula is
  *       invariant under a common scale, so normalising them changes nothing).
@@ -390,10 +398,16 @@ int orc_partition(const double* E, const int32_t* g, const double* E_vib, int64_
  * A is float64 (A_f32 == 0) or float32.
  * ------------------------------------------------------------------------ */
 
-static int window(double nu, double nu_min, double dnu, int64_t n_grid, double cut,
+static int window(double nu, double nu_min, double dnu, int64_t n_grid, double cut, double wl_unit,
                   int64_t* lo, int64_t* hi) {
-  double a = ceil(((nu - cut) - nu_min) / dnu);
-  double b = floor(((nu + cut) - nu_min) / dnu);
+  double a, b;
+  if (wl_unit > 0.0) {  /* R21: nu_min, dnu are lambda_min, dlambda */
+    a = ceil((wl_unit / (nu + cut) - nu_min) / dnu);
+    b = nu - cut > 0.0 ? floor((wl_unit / (nu - cut) - nu_min) / dnu) : (double)(n_grid - 1);
+  } else {
+    a = ceil(((nu - cut) - nu_min) / dnu);
+    b = floor(((nu + cut) - nu_min) / dnu);
+  }
   if (b < 0.0 || a > (double)(n_grid - 1) || a > b) return 0;
   *lo = a < 0.0 ? 0 : (int64_t)a;
   *hi = b > (double)(n_grid - 1) ? n_grid - 1 : (int64_t)b;
@@ -403,7 +417,7 @@ static int window(double nu, double nu_min, double dnu, int64_t n_grid, double c
 int orc_line_intensities(const double* E, const int32_t* g, const double* E_vib, int64_t n_states,
                          const int32_t* upper, const int32_t* lower, const void* A, int A_f32, int64_t n,
                          double T, double T_vib, double Q,
-                         double nu_min, double dnu, int64_t n_grid, double cut, double threshold,
+                         double nu_min, double dnu, int64_t n_grid, double cut, double threshold, double wl_unit,
                          double* nu_out, double* I_out, uint8_t* keep, int64_t* ilo, int64_t* ihi) {
   if (!(T > 0.0) || !(Q > 0.0) || !(dnu > 0.0) || cut < 0.0 || n_grid < 1) return ORC_ERR_ARG;
   const double c2 = orc_c2();
@@ -418,7 +432,7 @@ int orc_line_intensities(const double* E, const int32_t* g, const double* E_vib,
     nu_out[t] = nu;
     if (!(nu > 0.0)) continue;                                  /* R7, R15 */
     int64_t lo, hi;
-    if (!window(nu, nu_min, dnu, n_grid, cut, &lo, &hi)) continue;
+    if (!window(nu, nu_min, dnu, n_grid, cut, wl_unit, &lo, &hi)) continue;
     double gu = (double)g[u];
     double pref = gu * a / (8.0 * ORC_PI * ORC_C * nu * nu);
     double I;
@@ -509,7 +523,8 @@ int orc_partition_density(const double* E, const int32_t* g, const double* E_vib
 int orc_intensities(int emission, const double* E, const int32_t* g, const double* E_vib, const double* n_vib,
                     int64_t n_states, const int32_t* upper, const int32_t* lower, const void* A, int A_f32, int64_t n,
                     double T, double T_vib, double Q, double nu_min, double dnu, int64_t n_grid, double cut,
-                    double threshold, double* nu_out, double* I_out, uint8_t* keep, int64_t* ilo, int64_t* ihi) {
+                    double threshold, double wl_unit, double* nu_out, double* I_out, uint8_t* keep, int64_t* ilo,
+                    int64_t* ihi) {
   if (!(T > 0.0) || !(Q > 0.0) || !(dnu > 0.0) || cut < 0.0 || n_grid < 1) return ORC_ERR_ARG;
   if ((n_vib || T_vib > 0.0) && !E_vib) return ORC_ERR_ARG;
   if (n_vib && T_vib > 0.0) return ORC_ERR_ARG;
@@ -524,7 +539,7 @@ int orc_intensities(int emission, const double* E, const int32_t* g, const doubl
     nu_out[t] = nu;
     if (!(nu > 0.0)) continue;                                  /* R7, R15 */
     int64_t lo, hi;
-    if (!window(nu, nu_min, dnu, n_grid, cut, &lo, &hi)) continue;
+    if (!window(nu, nu_min, dnu, n_grid, cut, wl_unit, &lo, &hi)) continue;
     double val, p;
     int st;
     if (emission) {
@@ -589,24 +604,32 @@ void orc_scale_intensities(const double* I, const uint8_t* keep, int64_t n, int3
   for (int64_t t = 0; t < n; ++t) I_s[t] = keep[t] ? (float)ldexp(I[t], -k) : 0.0f;
 }
 
-/* R11: kept lines in ascending (nu bit pattern, index) order. */
+/* R11: kept lines in ascending (nu bit pattern, index) order; on a wavelength grid (R21) in
+ * descending nu bit pattern, ties by ascending index. */
 static const double* g_sort_nu;
+static int g_sort_desc;
 static int cmp_line(const void* pa, const void* pb) {
   int64_t a = *(const int64_t*)pa, b = *(const int64_t*)pb;
   uint64_t ka, kb;
   memcpy(&ka, &g_sort_nu[a], 8);
   memcpy(&kb, &g_sort_nu[b], 8);
-  if (ka != kb) return ka < kb ? -1 : 1;
+  if (ka != kb) return (ka < kb) != g_sort_desc ? -1 : 1;
   return a < b ? -1 : (a > b);
 }
 
-int64_t orc_sorted_order(const double* nu, const uint8_t* keep, int64_t n, int64_t* perm) {
+int64_t orc_sorted_order(const double* nu, const uint8_t* keep, int64_t n, double wl_unit, int64_t* perm) {
   int64_t m = 0;
   for (int64_t t = 0; t < n; ++t)
     if (keep[t]) perm[m++] = t;
   g_sort_nu = nu;
+  g_sort_desc = wl_unit > 0.0;
   qsort(perm, (size_t)m, sizeof(int64_t), cmp_line);
   return m;
+}
+
+/* Grid point i as a wavenumber: nu_min + i dnu, or U / (lambda_min + i dlambda) (R21). */
+static double grid_nu(double g0, double dg, int64_t i, double wl_unit) {
+  return wl_unit > 0.0 ? wl_unit / (g0 + (double)i * dg) : g0 + (double)i * dg;
 }
 
 /* Segment binning: for grid segments [s*S, (s+1)*S), the first sorted line whose
@@ -653,7 +676,8 @@ void orc_widths(int kind, const double* nu, const float* gamma_ref, const float*
 
 int orc_cross_section(int kind, const double* nu, const double* I, const double* alpha, const double* gamma,
                       const uint8_t* keep, const int64_t* ilo, const int64_t* ihi, int64_t n,
-                      double nu_min, double dnu, int64_t n_grid, double* sigma) {
+                      double nu_min, double dnu, int64_t n_grid, double wl_unit, double* sigma) {
+  if (wl_unit > 0.0 && (kind & ORC_BINNED) && kind < ORC_PV_THOMPSON) return ORC_ERR_ARG;
   if (!gl_ready) gl_init();
   for (int64_t i = 0; i < n_grid; ++i) sigma[i] = 0.0;
   int64_t nblk = 256;
@@ -667,7 +691,7 @@ int orc_cross_section(int kind, const double* nu, const double* I, const double*
       if (!keep[t] || ihi[t] < a0 || ilo[t] > a1) continue;
       int64_t lo = ilo[t] > a0 ? ilo[t] : a0, hi = ihi[t] < a1 ? ihi[t] : a1;
       for (int64_t i = lo; i <= hi; ++i) {
-        double x = (nu_min + (double)i * dnu) - nu[t];
+        double x = grid_nu(nu_min, dnu, i, wl_unit) - nu[t];
         sigma[i] += I[t] * prof_point(kind, x, dnu, alpha[t], gamma[t]);
       }
     }
@@ -680,7 +704,8 @@ int orc_cross_section(int kind, const double* nu, const double* I, const double*
  * transition-index order. */
 int orc_cross_section_window(int kind, const double* nu, const double* I, const double* alpha, const double* gamma,
                              const uint8_t* keep, const int64_t* ilo, const int64_t* ihi, int64_t n,
-                             double nu_min, double dnu, int64_t i0, int64_t m, double* sigma) {
+                             double nu_min, double dnu, int64_t i0, int64_t m, double wl_unit, double* sigma) {
+  if (wl_unit > 0.0 && (kind & ORC_BINNED) && kind < ORC_PV_THOMPSON) return ORC_ERR_ARG;
   if (!gl_ready) gl_init();
   for (int64_t j = 0; j < m; ++j) sigma[j] = 0.0;
   int64_t nblk = m < 64 ? m : 64;
@@ -695,7 +720,7 @@ int orc_cross_section_window(int kind, const double* nu, const double* I, const 
       if (!keep[t] || ihi[t] < a0 || ilo[t] > a1) continue;
       int64_t lo = ilo[t] > a0 ? ilo[t] : a0, hi = ihi[t] < a1 ? ihi[t] : a1;
       for (int64_t i = lo; i <= hi; ++i) {
-        double x = (nu_min + (double)i * dnu) - nu[t];
+        double x = grid_nu(nu_min, dnu, i, wl_unit) - nu[t];
         sigma[i - i0] += I[t] * prof_point(kind, x, dnu, alpha[t], gamma[t]);
       }
     }
