@@ -24,10 +24,12 @@ int64_t launches_total();
 
 // Exact window / position arithmetic parameters (IEEE double, no contraction).
 struct GridP {
-  double nu_min, dnu, cut;
+  double nu_min, dnu, cut;        // on a wavelength grid nu_min, dnu hold lambda_min, dlambda
   int64_t n;
   double nu_keep_lo, nu_keep_hi;  // nu in [lo, hi] <=> window meets the grid (when exact_bounds)
   int exact_bounds;               // 0: evaluate the window per line
+  double wl_unit;                 // 0: wavenumber grid; U > 0: wavelength grid with nu = U / lambda
+  double nu_span_lo, nu_span_hi;  // every kept line has nu in [lo, hi] (the state-code prefilter)
 };
 
 struct SlotP {                    // one temperature pair
@@ -43,14 +45,18 @@ void launch_boltzmann(const pxc_states* st, const SlotP* slots_dev, int nslot, d
                       StateFast* sfast, double* qpart, double* qres, unsigned* err, cudaStream_t s,
                       const double* Ssum = nullptr, double* W_out = nullptr);
 
-// Per-state 16-bit energy codes for the intensity pass's prefilter: q = floor((E - Emin) inv_res)
+// Per-state 12-bit energy codes for the intensity pass's prefilter: q = floor((E - Emin) inv_res)
 // for finite E (q <= kCodeMax), kCodeNone otherwise.  For every finite E, Emin + (q - 1) / inv_res
 // <= E <= Emin + (q + 2) / inv_res, so nu = E_u - E_l lies within (q_u - q_l -+ 3) / inv_res.
-// (8-bit codes, small enough for one die's L2 half, measured slower: eight times coarser bounds
-// send ~14% of the lines to the full test instead of ~4%.)
-using code_t = uint16_t;
-constexpr int kCodeNone = 65535;
+// Two states share three bytes (state 2p: byte 3p and the low half of byte 3p + 1; state 2p + 1: the
+// high half of byte 3p + 1 and byte 3p + 2): 75 MB for 5e7 states, which the random gathers of the
+// pass find in L2 far more often than the 100 MB of 16-bit codes (measured 0.9 against 1.45 ms
+// per 1e8 lines of gathers), for ~5 % candidates instead of ~3 %.  (8-bit codes, small enough
+// for one die's L2 half, send ~14 % of the lines to the full test.)
+using code_t = uint8_t;
+constexpr int kCodeNone = 4095;
 constexpr int kCodeMax = kCodeNone - 1;
+inline size_t code_bytes(int64_t n_states) { return (size_t)((n_states + 1) / 2) * 3; }
 struct QuantHdr {
   double Emin, inv_res;
   float res_f;      // 1 / inv_res rounded up
@@ -96,9 +102,13 @@ struct BoundP {
   int mode;      // IMODE_*
   double c2_Td;  // c2 / T (T_rot), FP64
 };
+// Intensity pass of the cross-section path: prefilter (candidates per unit into cand_* / ccount,
+// which need max_lines entries and one count per unit) and exact selection (kept lines staged per
+// unit into kstage / istage, counts into ucount, FP64 intensities by transition index into Iv).
 void launch_lines_compact(const pxc_transitions* tr, int64_t ns, const code_t* code, const QuantHdr* qh,
                           const StateFast* sfast, const double2* srec,
                           const double* qres, const GridP& gp, double threshold, const BoundP& bp, int with_I,
+                          uint32_t* cand_t, uint64_t* cand_ul, uint64_t* cand_a, uint32_t* ccount,
                           uint64_t* kstage, uint32_t* istage, double* Iv, uint32_t* ucount, int64_t nunit,
                           unsigned long long* maxbits, unsigned* err, cudaStream_t s);
 void launch_compact_staged(const uint64_t* kstage, const uint32_t* istage, const uint32_t* uoff, int64_t nunit,
@@ -167,8 +177,12 @@ struct ProfP {
   unsigned* err;
   long long spin_limit;   // bound of the waits for staged records (clock cycles)
   long long drain_limit;  // bound of the final wait for copies still in flight after a timeout
+  double wl_unit;         // > 0: wavelength grid (nu_min, dnu hold lambda_min, dlambda)
 };
 void launch_profile(const ProfP& p, int tile, int grid_ctas, cudaStream_t s);
+// Profile accumulation on a wavelength grid: 128-point segments, one work item per CTA.
+constexpr int kSegWl = 128;
+void launch_profile_wl(const ProfP& p, int64_t max_items, cudaStream_t s);
 int profile_occupancy(int kind, int tile);
 int tile_seg(int tile);
 

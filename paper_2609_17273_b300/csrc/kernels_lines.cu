@@ -16,15 +16,37 @@ int64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
 __device__ __forceinline__ void set_err(unsigned* err, unsigned bits) { atomicOr(err, bits); }
 
 // Window of grid indices of a line (R8): ceil((nu - cut - nu_min)/dnu), floor((nu + cut - nu_min)/dnu),
-// plain IEEE double with explicit rounding intrinsics so no contraction can change a tie.
+// plain IEEE double with explicit rounding intrinsics so no contraction can change a tie.  On a
+// wavelength grid (R21: lambda_i = lambda_min + i dlambda, nu_i = U / lambda_i) the points with
+// |nu_i - nu| <= cut are those with U/(nu + cut) <= lambda_i <= U/(nu - cut):
+// ceil((U/(nu + cut) - lambda_min)/dlambda) .. floor((U/(nu - cut) - lambda_min)/dlambda), the
+// last point when nu <= cut.
 __device__ __forceinline__ bool exact_window(double nu, const GridP& gp, int64_t* lo, int64_t* hi) {
-  double a = ceil(__ddiv_rn(__dsub_rn(__dsub_rn(nu, gp.cut), gp.nu_min), gp.dnu));
-  double b = floor(__ddiv_rn(__dsub_rn(__dadd_rn(nu, gp.cut), gp.nu_min), gp.dnu));
+  double a, b;
+  if (gp.wl_unit > 0.0) {
+    a = ceil(__ddiv_rn(__dsub_rn(__ddiv_rn(gp.wl_unit, __dadd_rn(nu, gp.cut)), gp.nu_min), gp.dnu));
+    b = __dsub_rn(nu, gp.cut) > 0.0
+            ? floor(__ddiv_rn(__dsub_rn(__ddiv_rn(gp.wl_unit, __dsub_rn(nu, gp.cut)), gp.nu_min), gp.dnu))
+            : (double)(gp.n - 1);
+  } else {
+    a = ceil(__ddiv_rn(__dsub_rn(__dsub_rn(nu, gp.cut), gp.nu_min), gp.dnu));
+    b = floor(__ddiv_rn(__dsub_rn(__dadd_rn(nu, gp.cut), gp.nu_min), gp.dnu));
+  }
   double top = (double)(gp.n - 1);
   if (!(b >= 0.0) || a > top || a > b) return false;
   *lo = a < 0.0 ? 0 : (int64_t)a;
   *hi = b > top ? gp.n - 1 : (int64_t)b;
   return true;
+}
+
+// Sort key of a kept line (nu > 0): its bit pattern (ascending nu, R11), or the complement on a
+// wavelength grid (descending nu = ascending wavelength, R21); the stable sort breaks ties by index.
+__device__ __forceinline__ uint64_t line_key(double nu, const GridP& gp) {
+  const uint64_t b = (uint64_t)__double_as_longlong(nu);
+  return gp.wl_unit > 0.0 ? ~b & 0x7fffffffffffffffull : b;
+}
+__device__ __forceinline__ double key_nu(uint64_t k, const GridP& gp) {
+  return __longlong_as_double((long long)(gp.wl_unit > 0.0 ? ~k & 0x7fffffffffffffffull : k));
 }
 
 __device__ __forceinline__ bool window_meets_grid(double nu, const GridP& gp) {
@@ -254,19 +276,25 @@ __device__ __forceinline__ QuantHdr quant_header(const unsigned long long* words
   return h;
 }
 
+__device__ __forceinline__ int quant_code(double e, const QuantHdr& h) {
+  if (!h.enabled || !isfinite(e)) return kCodeNone;
+  const double x = floor((e - h.Emin) * h.inv_res);
+  return x < 0.0 ? 0 : (x > (double)kCodeMax ? kCodeMax : (int)x);
+}
+
+// One thread per pair of states: the two 12-bit codes in three bytes.
 __global__ void __launch_bounds__(256) k_state_quant(const double* __restrict__ E, int64_t n,
                                                      const unsigned long long* __restrict__ words,
                                                      code_t* __restrict__ code, QuantHdr* __restrict__ hdr) {
   const QuantHdr h = quant_header(words);
   if (blockIdx.x == 0 && threadIdx.x == 0) *hdr = h;
-  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
-    const double e = E[s];
-    int q = kCodeNone;
-    if (h.enabled && isfinite(e)) {
-      const double x = floor((e - h.Emin) * h.inv_res);
-      q = x < 0.0 ? 0 : (x > (double)kCodeMax ? kCodeMax : (int)x);
-    }
-    code[s] = (code_t)q;
+  const int64_t np = (n + 1) / 2;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
+    const int q0 = quant_code(E[2 * p], h);
+    const int q1 = 2 * p + 1 < n ? quant_code(E[2 * p + 1], h) : kCodeNone;
+    code[3 * p] = (code_t)(q0 & 0xff);
+    code[3 * p + 1] = (code_t)((q0 >> 8) | ((q1 & 0xf) << 4));
+    code[3 * p + 2] = (code_t)(q1 >> 4);
   }
 }
 
@@ -327,7 +355,7 @@ __global__ void __launch_bounds__(kThreadsI) k_lines(const int32_t* __restrict__
         if (keep) I = num / den;
       }
       if (keep) {
-        kk = (uint64_t)__double_as_longlong(nu);
+        kk = line_key(nu, gp);
         ++kept;
         unsigned long long ib = (unsigned long long)__double_as_longlong(fabs(I));
         mx = ib > mx ? ib : mx;
@@ -378,8 +406,8 @@ void launch_lines(const pxc_transitions* tr, const int32_t* g, int64_t ns, const
 // LTE (b_l - b_u = b_l (1 - e^{-c2 nu/T})) and m = 1 for two temperatures, evaluated in log2
 // units with a 1e-3 margin that covers every FP32 rounding in it.
 //
-// Before any 16-byte state record is read, a prefilter on the 16-bit state codes (a table of
-// 2 bytes per state, small enough to stay in L2 for 5e7 states) rejects lines whose nu is
+// Before any 16-byte state record is read, a prefilter on the 12-bit state codes (1.5 bytes per
+// state, 75 MB for 5e7 states, mostly found in L2) rejects lines whose nu is
 // certainly outside the kept window, and, for LTE with a threshold, lines whose intensity is
 // certainly below it: nu_lo = (d - 3) res, nu_hi = (d + 3) res with d = q_u - q_l, b_l <=
 // exp(-c2 E_lo(q_l) / T), g_u <= max g.  Only the surviving candidates gather their states.
@@ -399,11 +427,17 @@ __device__ __forceinline__ uint32_t block_rank(bool flag, uint32_t* wsum, uint32
   return before + __popc(m & ((1u << lane) - 1u));
 }
 
-// Code load kept in L2 with the evict-last policy (the state codes are re-read at random).
-__device__ __forceinline__ int ld_code(const code_t* p, uint64_t pol) {
+// 12-bit code of state s (two byte loads of one sector, kept in L2 with the evict-last policy: the
+// state codes are re-read at random).
+__device__ __forceinline__ int ld_byte(const code_t* p, uint64_t pol) {
   unsigned short v;
-  asm volatile("ld.global.nc.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(pol));
+  asm volatile("ld.global.nc.L2::cache_hint.u8 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(pol));
   return (int)v;
+}
+__device__ __forceinline__ int ld_code(const code_t* tab, int32_t s, uint64_t pol) {
+  const code_t* p = tab + 3 * (int64_t)(s >> 1);
+  if (s & 1) return (ld_byte(p + 1, pol) >> 4) | (ld_byte(p + 2, pol) << 4);
+  return ld_byte(p, pol) | ((ld_byte(p + 1, pol) & 0xf) << 8);
 }
 
 // Per-block constants of the compacting intensity pass (computed once per CTA by one thread).
@@ -413,200 +447,238 @@ struct LinesConst {
   int dlo, dhi, pre, pre_thr;
 };
 
-// One warp owns a unit of kUnitLines consecutive lines and walks it 32 lines at a time; its
-// candidates queue (in line order) in a per-warp buffer that is drained 32 at a time, so the
-// state gathers and the FP64 test run on full warps and no CTA barrier is needed per round.
-// Kept lines go to the unit's own staging range in line order, counted per unit.
-constexpr int kCandBuf = 64;
+__device__ LinesConst lines_const(const code_t* code, const QuantHdr* qhp, const double* qres, const GridP& gp,
+                                  double threshold, const BoundP& bp, int with_I) {
+  LinesConst c{};
+  c.invQ = with_I ? qres[3] : 0.0;
+  c.l2invQ = with_I ? (float)log2(c.invQ) : 0.f;
+  QuantHdr qh{};
+  if (code) qh = *qhp;
+  const double wl = gp.exact_bounds ? gp.nu_keep_lo : gp.nu_span_lo;
+  const double wh = gp.exact_bounds ? gp.nu_keep_hi : gp.nu_span_hi;
+  // the codes are used when their resolution is at most 1/16 of the kept nu range (a list
+  // whose energies span far more than the window gains nothing from them)
+  c.pre = code != nullptr && qh.enabled && (wh - wl) * qh.inv_res >= 16.0;
+  // the code bound on b_l holds for LTE absorption only
+  c.pre_thr = c.pre && with_I && threshold > 0.0 && bp.lte && bp.mode == IMODE_ABS;
+  c.dlo = INT_MIN;
+  c.dhi = INT_MAX;
+  if (c.pre) {
+    // kept lines have nu in [wl, wh] (infinite ends: none kept); widen by two grid steps,
+    // a relative 1e-9 and four code steps
+    const double a = isinf(wl) ? (wl > 0 ? 2e9 : -2e9)
+                               : floor((wl - 2.0 * gp.dnu - 1e-9 * fabs(wl)) * qh.inv_res) - 4.0;
+    const double b = isinf(wh) ? (wh > 0 ? 2e9 : -2e9)
+                               : ceil((wh + 2.0 * gp.dnu + 1e-9 * fabs(wh)) * qh.inv_res) + 4.0;
+    c.dlo = a < -1e9 ? -1000000000 : (a > 1e9 ? 1000000000 : (int)a);
+    c.dhi = b > 1e9 ? 1000000000 : (b < -1e9 ? -1000000000 : (int)b);
+  }
+  c.lo_scale = qh.res_f * 0.99999f;
+  c.hi_scale = qh.res_f * 1.00001f;
+  c.Emin_f = qh.Emin_f;
+  c.log2_gmax = qh.log2_gmax;
+  return c;
+}
 
-__global__ void __launch_bounds__(kThreadsI) k_lines_c(const int32_t* __restrict__ up, const int32_t* __restrict__ lo,
-                                                       const void* __restrict__ Av, int A32, int64_t n,
-                                                       const code_t* __restrict__ code,
-                                                       const QuantHdr* __restrict__ qhp,
-                                                       const StateFast* __restrict__ sfast,
-                                                       const double2* __restrict__ srec, int64_t ns,
-                                                       const double* __restrict__ qres, GridP gp, double threshold,
-                                                       BoundP bp, int with_I, uint64_t* __restrict__ kstage,
-                                                       uint32_t* __restrict__ istage, double* __restrict__ Iv,
-                                                       uint32_t* __restrict__ ucount, int64_t nunit,
-                                                       unsigned long long* __restrict__ maxbits, unsigned* err) {
+// Loads line t (streaming: upper, lower, A) and decides whether it is a candidate: valid ids and,
+// when the codes are on, a code-bound nu inside the kept window and (LTE with a threshold) a code
+// bound on |I| at or above the threshold.  Bad ids and non-finite A are reported in `bad`.
+__device__ __forceinline__ bool line_candidate(int64_t t, const int32_t* __restrict__ up,
+                                               const int32_t* __restrict__ lo, const void* __restrict__ Av, int A32,
+                                               int64_t ns, const code_t* __restrict__ code, const LinesConst& c,
+                                               const BoundP& bp, uint64_t pol, int32_t* u_out, int32_t* l_out,
+                                               unsigned long long* ab_out, unsigned* bad) {
+  const int32_t u = __ldcs(up + t), l = __ldcs(lo + t);
+  float Af;
+  bool finite;
+  unsigned long long ab;
+  if (A32) {
+    Af = __ldcs((const float*)Av + t);
+    ab = __float_as_uint(Af);
+    finite = (ab & 0x7f800000u) != 0x7f800000u;
+  } else {
+    const double A = __ldcs((const double*)Av + t);
+    ab = (unsigned long long)__double_as_longlong(A);
+    finite = (ab & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
+    Af = (float)A;
+  }
+  *u_out = u;
+  *l_out = l;
+  *ab_out = ab;
+  if (u < 0 || u >= ns || l < 0 || l >= ns) {
+    *bad |= ERRB_ID;
+    return false;
+  }
+  if (!finite) *bad |= ERRB_NONFINITE;
+  if (!c.pre) return true;
+  const int qu = ld_code(code, u, pol), ql = ld_code(code, l, pol);
+  if (qu == kCodeNone || ql == kCodeNone) return true;
+  const int d = qu - ql;
+  if (d < c.dlo || d > c.dhi) return false;
+  if (c.pre_thr && d > 3) {
+    const float kl2e = 1.4426950408889634f;
+    const float nul = (float)(d - 3) * c.lo_scale, nuh = (float)(d + 3) * c.hi_scale;
+    const float m = fminf(1.f, bp.c2_T * nuh);
+    const float Elo = fmaf((float)(ql - 1), ql >= 1 ? c.lo_scale : c.hi_scale, c.Emin_f);
+    const float lbl = -(bp.c2_T * kl2e) * Elo;  // log2 of the upper bound of b_l
+    const float Pb = Af * m / (nul * nul);
+    if (__log2f(Pb) + c.log2_gmax + lbl + c.l2invQ < bp.log2_thr - 1e-6f * fabsf(lbl)) return false;
+  }
+  return true;
+}
+
+// The intensity pass of the cross-section path in two kernels.  The prefilter streams the lines
+// (one warp per unit of kUnitLines consecutive lines) and writes each unit's candidates, in line
+// order, to the unit's range of three candidate arrays; it holds few registers, so the random
+// code gathers it waits on have the whole SM's worth of warps in flight.  The exact pass then
+// takes each unit's candidates 32 at a time on full warps: the 16-byte state records, exact nu and
+// window, the FP32 bound with the exact log2 b, then the FP64 test |num| >= S_min nu^2 and
+// I = num / nu^2; kept lines go to the unit's staging range in line order, counted per unit.
+// When the codes are off (a list whose energies span far more than the kept window) the exact
+// pass reads the lines directly and the prefilter does nothing.
+__global__ void __launch_bounds__(kThreadsI, 8) k_lines_pre(const int32_t* __restrict__ up,
+                                                         const int32_t* __restrict__ lo,
+                                                         const void* __restrict__ Av, int A32, int64_t n,
+                                                         const code_t* __restrict__ code,
+                                                         const QuantHdr* __restrict__ qhp, int64_t ns,
+                                                         const double* __restrict__ qres, GridP gp, double threshold,
+                                                         BoundP bp, int with_I, uint32_t* __restrict__ cand_t,
+                                                         uint64_t* __restrict__ cand_ul, uint64_t* __restrict__ cand_a,
+                                                         uint32_t* __restrict__ ccount, int64_t nunit, unsigned* err) {
+  __shared__ LinesConst kc;
+  if (threadIdx.x == 0) kc = lines_const(code, qhp, qres, gp, threshold, bp, with_I);
+  __syncthreads();
+  const LinesConst c = kc;
+  if (!c.pre) return;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t unit = (int64_t)blockIdx.x * (kThreadsI / 32) + (threadIdx.x >> 5);
+  if (unit >= nunit) return;
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  const int64_t ubase = unit * kUnitLines;
+  unsigned bad = 0;
+  uint32_t nb = 0;
+  for (int r = 0; r < kUnitLines / 32; ++r) {
+    const int64_t t = ubase + r * 32 + lane;
+    bool cand = false;
+    int32_t u = 0, l = 0;
+    unsigned long long ab = 0;
+    if (t < n) cand = line_candidate(t, up, lo, Av, A32, ns, code, c, bp, pol, &u, &l, &ab, &bad);
+    const unsigned cm = __ballot_sync(0xffffffffu, cand);
+    if (cand) {
+      const int64_t o = ubase + nb + __popc(cm & lt);
+      cand_t[o] = (uint32_t)t;
+      cand_ul[o] = ((uint64_t)(uint32_t)u << 32) | (uint32_t)l;
+      cand_a[o] = ab;
+    }
+    nb += __popc(cm);
+  }
+  if (lane == 0) ccount[unit] = nb;
+  if (bad) set_err(err, bad);
+}
+
+__global__ void __launch_bounds__(kThreadsI) k_lines_exact(const int32_t* __restrict__ up,
+                                                           const int32_t* __restrict__ lo,
+                                                           const void* __restrict__ Av, int A32, int64_t n,
+                                                           const code_t* __restrict__ code,
+                                                           const QuantHdr* __restrict__ qhp,
+                                                           const StateFast* __restrict__ sfast,
+                                                           const double2* __restrict__ srec, int64_t ns,
+                                                           const double* __restrict__ qres, GridP gp,
+                                                           double threshold, BoundP bp, int with_I,
+                                                           const uint32_t* __restrict__ cand_t,
+                                                           const uint64_t* __restrict__ cand_ul,
+                                                           const uint64_t* __restrict__ cand_a,
+                                                           const uint32_t* __restrict__ ccount,
+                                                           uint64_t* __restrict__ kstage, uint32_t* __restrict__ istage,
+                                                           double* __restrict__ Iv, uint32_t* __restrict__ ucount,
+                                                           int64_t nunit, unsigned long long* __restrict__ maxbits,
+                                                           unsigned* err) {
   constexpr int NW = kThreadsI / 32;
   __shared__ LinesConst kc;
-  __shared__ uint32_t cb_t[NW][kCandBuf];
-  __shared__ int32_t cb_u[NW][kCandBuf], cb_l[NW][kCandBuf];
-  __shared__ unsigned long long cb_A[NW][kCandBuf];  // A: FP32 bits (A32) or FP64 bits
   __shared__ unsigned long long wmax[NW];
-  if (threadIdx.x == 0) {
-    LinesConst c{};
-    c.invQ = with_I ? qres[3] : 0.0;
-    c.l2invQ = with_I ? (float)log2(c.invQ) : 0.f;
-    QuantHdr qh{};
-    if (code) qh = *qhp;
-    const double nu_max = gp.nu_min + (double)(gp.n - 1) * gp.dnu;
-    const double wl = gp.exact_bounds ? gp.nu_keep_lo : fmax(gp.nu_min - gp.cut, 0.0);
-    const double wh = gp.exact_bounds ? gp.nu_keep_hi : nu_max + gp.cut;
-    // the codes are used when their resolution is at most 1/16 of the kept nu range (a list
-    // whose energies span far more than the window gains nothing from them)
-    c.pre = code != nullptr && qh.enabled && (wh - wl) * qh.inv_res >= 16.0;
-    // the code bound on b_l holds for LTE absorption only
-    c.pre_thr = c.pre && with_I && threshold > 0.0 && bp.lte && bp.mode == IMODE_ABS;
-    c.dlo = INT_MIN;
-    c.dhi = INT_MAX;
-    if (c.pre) {
-      // kept lines have nu in [wl, wh] (infinite ends: none kept); widen by two grid steps,
-      // a relative 1e-9 and four code steps
-      const double a = isinf(wl) ? (wl > 0 ? 2e9 : -2e9)
-                                 : floor((wl - 2.0 * gp.dnu - 1e-9 * fabs(wl)) * qh.inv_res) - 4.0;
-      const double b = isinf(wh) ? (wh > 0 ? 2e9 : -2e9)
-                                 : ceil((wh + 2.0 * gp.dnu + 1e-9 * fabs(wh)) * qh.inv_res) + 4.0;
-      c.dlo = a < -1e9 ? -1000000000 : (a > 1e9 ? 1000000000 : (int)a);
-      c.dhi = b > 1e9 ? 1000000000 : (b < -1e9 ? -1000000000 : (int)b);
-    }
-    c.lo_scale = qh.res_f * 0.99999f;
-    c.hi_scale = qh.res_f * 1.00001f;
-    c.Emin_f = qh.Emin_f;
-    c.log2_gmax = qh.log2_gmax;
-    kc = c;
-  }
+  if (threadIdx.x == 0) kc = lines_const(code, qhp, qres, gp, threshold, bp, with_I);
   __syncthreads();
   const LinesConst c = kc;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   const int64_t unit = (int64_t)blockIdx.x * NW + warp;
   const long long lo_bits = __double_as_longlong(gp.nu_keep_lo), hi_bits = __double_as_longlong(gp.nu_keep_hi);
-  const float kl2e = 1.4426950408889634f;
-  uint64_t pol;
-  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
   unsigned long long mx = 0;
   unsigned bad = 0;
   uint32_t run = 0;  // kept lines of this unit so far
-  int nb = 0;        // queued candidates
   const int64_t ubase = unit * kUnitLines;
-
-  // Exact selection of the first `cnt` queued candidates (lane i takes entry i), in queue order.
-  auto drain = [&](int cnt) {
-    bool keep = false;
-    double nu = 0.0, I = 0.0;
-    uint32_t t = 0;
-    if (lane < cnt) {
-      t = cb_t[warp][lane];
-      const int32_t u = cb_u[warp][lane], l = cb_l[warp][lane];
-      const unsigned long long ab = cb_A[warp][lane];
-      const double A = A32 ? (double)__uint_as_float((unsigned)ab) : __longlong_as_double((long long)ab);
-      const StateFast fu = sfast[u], fl = sfast[l];
-      nu = __dsub_rn(fu.E, fl.E);
-      if (gp.exact_bounds) {
-        const long long nbits = __double_as_longlong(nu);
-        keep = nbits >= lo_bits && nbits <= hi_bits;
-      } else {
-        int64_t a, b;
-        keep = nu > 0.0 && exact_window(nu, gp, &a, &b);
-      }
-      if (keep && with_I) {
-        if (threshold > 0.0) {
-          // conservative FP32 log2 bound on |value| (see line_value)
-          const float nuf = (float)nu;
-          float P, lbb;
-          if (bp.mode == IMODE_EMISSION) {
-            P = (float)fu.g * (float)A * nuf * (float)kTwoHC2;
-            lbb = fu.lb;
-          } else {
-            const float m = bp.lte ? fminf(1.f, bp.c2_T * nuf) : 1.f;
-            P = (float)fu.g * (float)A * m / (nuf * nuf);
-            lbb = fmaxf(fu.lb, fl.lb);
-          }
-          if (__log2f(P) + lbb + c.l2invQ < bp.log2_thr) keep = false;
-        }
-        if (keep) {
-          double num, den;
-          line_value(bp.mode, bp.c2_Td, (double)fu.g, A, c.invQ, srec[l].y, srec[u].y, nu, &num, &den);
-          keep = fabs(num) >= threshold * den;
-          if (keep) I = num / den;
-        }
-      }
-    }
-    const unsigned kb = __ballot_sync(0xffffffffu, keep);
-    if (keep) {
-      const int64_t o = ubase + run + __popc(kb & lt);
-      kstage[o] = (uint64_t)__double_as_longlong(nu);
-      istage[o] = t;
-      if (with_I) {
-        Iv[t] = I;
-        const unsigned long long ib = (unsigned long long)__double_as_longlong(fabs(I));
-        mx = ib > mx ? ib : mx;
-      }
-    }
-    run += __popc(kb);
-  };
-
   if (unit < nunit) {
-    for (int r = 0; r < kUnitLines / 32; ++r) {
-      const int64_t t = ubase + r * 32 + lane;
-      bool cand = false;
-      int32_t u = 0, l = 0;
-      unsigned long long ab = 0;
-      if (t < n) {
-        u = __ldcs(up + t);
-        l = __ldcs(lo + t);
-        float Af;
-        bool finite;
-        if (A32) {
-          Af = __ldcs((const float*)Av + t);
-          ab = __float_as_uint(Af);
-          finite = (ab & 0x7f800000u) != 0x7f800000u;
+    // candidates of this unit: from the prefilter, or every line when the codes are off
+    const int64_t ncand = c.pre ? (int64_t)ccount[unit] : min((int64_t)kUnitLines, n - ubase);
+    for (int64_t j0 = 0; j0 < ncand; j0 += 32) {
+      bool keep = false;
+      double nu = 0.0, I = 0.0;
+      uint32_t t = 0;
+      if (j0 + lane < ncand) {
+        int32_t u, l;
+        unsigned long long ab;
+        bool ok = true;
+        if (c.pre) {
+          const int64_t o = ubase + j0 + lane;
+          t = cand_t[o];
+          const uint64_t ul = cand_ul[o];
+          u = (int32_t)(ul >> 32);
+          l = (int32_t)(uint32_t)ul;
+          ab = cand_a[o];
         } else {
-          const double A = __ldcs((const double*)Av + t);
-          ab = (unsigned long long)__double_as_longlong(A);
-          finite = (ab & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
-          Af = (float)A;
+          t = (uint32_t)(ubase + j0 + lane);
+          ok = line_candidate(t, up, lo, Av, A32, ns, nullptr, c, bp, 0, &u, &l, &ab, &bad);
         }
-        if (u < 0 || u >= ns || l < 0 || l >= ns) {
-          bad |= ERRB_ID;
-        } else {
-          if (!finite) bad |= ERRB_NONFINITE;
-          cand = true;
-          if (c.pre) {
-            const int qu = ld_code(code + u, pol), ql = ld_code(code + l, pol);
-            if (qu != kCodeNone && ql != kCodeNone) {
-              const int d = qu - ql;
-              if (d < c.dlo || d > c.dhi) {
-                cand = false;
-              } else if (c.pre_thr && d > 3) {
-                const float nul = (float)(d - 3) * c.lo_scale, nuh = (float)(d + 3) * c.hi_scale;
-                const float m = fminf(1.f, bp.c2_T * nuh);
-                const float Elo = fmaf((float)(ql - 1), ql >= 1 ? c.lo_scale : c.hi_scale, c.Emin_f);
-                const float lbl = -(bp.c2_T * kl2e) * Elo;  // log2 of the upper bound of b_l
-                const float Pb = Af * m / (nul * nul);
-                if (__log2f(Pb) + c.log2_gmax + lbl + c.l2invQ < bp.log2_thr - 1e-6f * fabsf(lbl)) cand = false;
+        if (ok) {
+          const double A = A32 ? (double)__uint_as_float((unsigned)ab) : __longlong_as_double((long long)ab);
+          const StateFast fu = sfast[u], fl = sfast[l];
+          nu = __dsub_rn(fu.E, fl.E);
+          if (gp.exact_bounds) {
+            const long long nbits = __double_as_longlong(nu);
+            keep = nbits >= lo_bits && nbits <= hi_bits;
+          } else {
+            int64_t a, b;
+            keep = nu > 0.0 && exact_window(nu, gp, &a, &b);
+          }
+          if (keep && with_I) {
+            if (threshold > 0.0) {
+              // conservative FP32 log2 bound on |value| (see line_value)
+              const float nuf = (float)nu;
+              float P, lbb;
+              if (bp.mode == IMODE_EMISSION) {
+                P = (float)fu.g * (float)A * nuf * (float)kTwoHC2;
+                lbb = fu.lb;
+              } else {
+                const float m = bp.lte ? fminf(1.f, bp.c2_T * nuf) : 1.f;
+                P = (float)fu.g * (float)A * m / (nuf * nuf);
+                lbb = fmaxf(fu.lb, fl.lb);
               }
+              if (__log2f(P) + lbb + c.l2invQ < bp.log2_thr) keep = false;
+            }
+            if (keep) {
+              double num, den;
+              line_value(bp.mode, bp.c2_Td, (double)fu.g, A, c.invQ, srec[l].y, srec[u].y, nu, &num, &den);
+              keep = fabs(num) >= threshold * den;
+              if (keep) I = num / den;
             }
           }
         }
       }
-      const unsigned cm = __ballot_sync(0xffffffffu, cand);
-      if (cand) {
-        const int p = nb + __popc(cm & lt);
-        cb_t[warp][p] = (uint32_t)t;
-        cb_u[warp][p] = u;
-        cb_l[warp][p] = l;
-        cb_A[warp][p] = ab;
-      }
-      nb += __popc(cm);
-      __syncwarp();
-      if (nb >= 32) {
-        drain(32);
-        __syncwarp();
-        if (lane < nb - 32) {
-          cb_t[warp][lane] = cb_t[warp][lane + 32];
-          cb_u[warp][lane] = cb_u[warp][lane + 32];
-          cb_l[warp][lane] = cb_l[warp][lane + 32];
-          cb_A[warp][lane] = cb_A[warp][lane + 32];
+      const unsigned kb = __ballot_sync(0xffffffffu, keep);
+      if (keep) {
+        const int64_t o = ubase + run + __popc(kb & lt);
+        kstage[o] = line_key(nu, gp);
+        istage[o] = t;
+        if (with_I) {
+          Iv[t] = I;
+          const unsigned long long ib = (unsigned long long)__double_as_longlong(fabs(I));
+          mx = ib > mx ? ib : mx;
         }
-        nb -= 32;
-        __syncwarp();
       }
+      run += __popc(kb);
     }
-    if (nb > 0) drain(nb);
     if (lane == 0) ucount[unit] = run;
   }
   if (bad) set_err(err, bad);
@@ -629,14 +701,18 @@ __global__ void __launch_bounds__(kThreadsI) k_lines_c(const int32_t* __restrict
 void launch_lines_compact(const pxc_transitions* tr, int64_t ns, const code_t* code, const QuantHdr* qh,
                           const StateFast* sfast, const double2* srec,
                           const double* qres, const GridP& gp, double threshold, const BoundP& bp, int with_I,
+                          uint32_t* cand_t, uint64_t* cand_ul, uint64_t* cand_a, uint32_t* ccount,
                           uint64_t* kstage, uint32_t* istage, double* Iv, uint32_t* ucount, int64_t nunit,
                           unsigned long long* maxbits, unsigned* err, cudaStream_t s) {
   if (nunit == 0) return;
   const int64_t nblk = (nunit + kThreadsI / 32 - 1) / (kThreadsI / 32);
-  k_lines_c<<<(unsigned)nblk, kThreadsI, 0, s>>>(tr->upper, tr->lower, tr->A, tr->A_is_f32, tr->n, code, qh, sfast,
-                                                 srec, ns, qres, gp, threshold, bp, with_I, kstage, istage, Iv,
-                                                 ucount, nunit, maxbits, err);
-  note_launches(1);
+  k_lines_pre<<<(unsigned)nblk, kThreadsI, 0, s>>>(tr->upper, tr->lower, tr->A, tr->A_is_f32, tr->n, code, qh, ns,
+                                                   qres, gp, threshold, bp, with_I, cand_t, cand_ul, cand_a, ccount,
+                                                   nunit, err);
+  k_lines_exact<<<(unsigned)nblk, kThreadsI, 0, s>>>(tr->upper, tr->lower, tr->A, tr->A_is_f32, tr->n, code, qh,
+                                                     sfast, srec, ns, qres, gp, threshold, bp, with_I, cand_t, cand_ul,
+                                                     cand_a, ccount, kstage, istage, Iv, ucount, nunit, maxbits, err);
+  note_launches(2);
 }
 
 // Copies each unit's staged kept lines to its offset (exclusive scan of the counts, total at
@@ -861,11 +937,13 @@ __global__ void __launch_bounds__(256) k_prepare(const uint64_t* __restrict__ sk
   const int k = Iv ? kexp[0] : 0;
   unsigned long long ev = 0, evnz = 0, nz = 0;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-    double nu = __longlong_as_double((long long)skey[j]);
+    double nu = key_nu(skey[j], gp);
     uint32_t t = sidx[j];
     int64_t a = 0, b = -1;
     exact_window(nu, gp, &a, &b);
-    double c = __ddiv_rn(__dsub_rn(nu, gp.nu_min), gp.dnu);
+    // position in grid steps: (nu - nu_min)/dnu, or (U/nu - lambda_min)/dlambda on a wavelength grid
+    const double coord = gp.wl_unit > 0.0 ? __ddiv_rn(gp.wl_unit, nu) : nu;
+    double c = __ddiv_rn(__dsub_rn(coord, gp.nu_min), gp.dnu);
     double fc = floor(c);
     float f = (float)__dsub_rn(c, fc);
     pos[j] = make_int4((int)fc, __float_as_int(f), (int)a, (int)b);
