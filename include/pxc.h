@@ -90,11 +90,18 @@ typedef struct {
   double P;              /* bar */
 } pxc_condition;
 
-/* Wavenumber grid nu_i = nu_min + i * dnu, i = 0 .. n-1 (Sec. 2.4.3). */
+/* Spectral grid (Sec. 2.4.3).  wl_unit == 0: wavenumbers nu_i = nu_min + i * dnu, i = 0 .. n-1.
+ * wl_unit > 0: wavelengths lambda_i = nu_min + i * dnu (the fields then hold lambda_min and
+ * dlambda) in the unit with nu = wl_unit / lambda: 1e7 for nm, 1e4 for um.  On a wavelength grid
+ * sigma is sampled at nu_i = wl_unit / lambda_i, the cut-off stays in cm^-1, the window of a line
+ * is i_lo = ceil((U/(nu + cut) - lambda_min)/dlambda), i_hi = floor((U/(nu - cut) - lambda_min)/
+ * dlambda) (the last point when nu <= cut), lines are ordered by descending nu (ties by index),
+ * and only the sampled kinds (0..3, 8..10) are accepted, forward only. */
 typedef struct {
   double nu_min;
   double dnu;
   int64_t n;
+  double wl_unit;
 } pxc_grid;
 
 /* Line profiles (Table profile). */
@@ -110,8 +117,18 @@ typedef enum {
   PXC_BINNED_GAUSS_DOPPLER = 4, /* erf / erfc differences */
   PXC_BINNED_GAUSS_HWHM = 5,
   PXC_BINNED_LORENTZ = 6,       /* arctangent difference */
-  PXC_BINNED_VOIGT = 7          /* composite 2-point Gauss-Legendre over the bin, subintervals of a
+  PXC_BINNED_VOIGT = 7,         /* composite 2-point Gauss-Legendre over the bin, subintervals of a
                                    quarter of the local width scale, at most 1024 per bin */
+  /* Pseudo-Voigt approximations (Table profile): a Lorentzian and a Gaussian of one common full
+   * width G, mixed with weights wL, wG, from the Voigt kind's Doppler and Lorentz widths (full
+   * widths fG = 2 alpha, fL = 2 gamma).  Sampled, forward only. */
+  PXC_PV_THOMPSON = 8,          /* Thompson, Cox, Hastings (1987): G from the fifth-power formula,
+                                   wL = 1.36603 r - 0.47719 r^2 + 0.11116 r^3, r = fL / G */
+  PXC_PV_OLIVERO = 9,           /* Olivero, Longbothum (1977) width G = 0.5346 fL + sqrt(0.2166 fL^2 + fG^2),
+                                   the same mixing */
+  PXC_PV_LIULIN = 10            /* Liu, Lin et al. (2001): width and both weights as cubic/analytic
+                                   functions of d = (fL - fG)/(fL + fG); wL + wG differs from 1 by
+                                   up to 0.73 % */
 } pxc_profile;
 
 typedef struct {
@@ -291,7 +308,8 @@ pxc_status pxc_get_timing(pxc_workspace* ws, cudaStream_t stream, double* ms, in
  *   tile 1: S = 256  (64 threads x 4 points, 64 lines per stage)
  *   tile 2: S = 1024 (128 threads x 8 points, 64 lines per stage)
  *   tile 3: S = 2048 (128 threads x 16 points, 128 lines per stage)
- * and every one gives the same sigma up to FP32 summation order.  The workspace
+ * and every one gives the same sigma up to FP32 summation order.  Wavelength grids always
+ * use 128-point segments.  The workspace
  * keeps one tile per profile kind for single-condition calls (batched = 0,
  * default tile 0) and one for batched tables (batched = 1, default tile 3). */
 #define PXC_NUM_TILES 4

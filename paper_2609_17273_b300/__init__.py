@@ -21,7 +21,12 @@ LIB_PATH = os.path.join(_HERE, "libpxc.so")
 
 PXC_GAUSS_DOPPLER, PXC_GAUSS_HWHM, PXC_LORENTZ, PXC_VOIGT = 0, 1, 2, 3
 PROFILES = {"gauss_doppler": 0, "gauss_hwhm": 1, "lorentz": 2, "voigt": 3,
-            "binned_gauss_doppler": 4, "binned_gauss_hwhm": 5, "binned_lorentz": 6, "binned_voigt": 7}
+            "binned_gauss_doppler": 4, "binned_gauss_hwhm": 5, "binned_lorentz": 6, "binned_voigt": 7,
+            "pv_thompson": 8, "pv_olivero": 9, "pv_liulin": 10}
+# Kinds whose widths include the pressure (Lorentz) width, so need gamma_ref and n_T.
+BROADENED = ("lorentz", "voigt", "binned_lorentz", "binned_voigt", "pv_thompson", "pv_olivero", "pv_liulin")
+# Wavelength units of a grid (nu = unit / lambda): pass as the grid's fourth element.
+WL_NM, WL_UM = 1e7, 1e4
 PXC_EXP_EMPTY = -2147483648
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_ID_RANGE", 3: "ERR_NONFINITE", 4: "ERR_OVERFLOW", 5: "ERR_TIMEOUT",
           6: "ERR_CUDA", 7: "ERR_CAPACITY"}
@@ -42,7 +47,8 @@ class pxc_condition(ctypes.Structure):
 
 
 class pxc_grid(ctypes.Structure):
-    _fields_ = [("nu_min", c_dbl), ("dnu", c_dbl), ("n", c_i64)]
+    """(nu_min, dnu, n[, wl_unit]): wavenumbers, or wavelengths in the unit wl_unit (1e7 nm, 1e4 um)."""
+    _fields_ = [("nu_min", c_dbl), ("dnu", c_dbl), ("n", c_i64), ("wl_unit", c_dbl)]
 
 
 class pxc_profile_args(ctypes.Structure):
@@ -82,6 +88,7 @@ ABI_FUNCTIONS = [
 # Profile-kernel tile configurations (segment width in grid points), as compiled into the library.
 NUM_TILES = 4
 TILE_SEGMENT_POINTS = (128, 256, 1024, 2048)
+BATCHED_DEFAULT_TILE = 3
 
 
 def load(path: str | None = None):
@@ -437,7 +444,7 @@ def pxc_cross_section_streamed(ws: Workspace, states: States, upper, lower, A, g
     """Host-resident (preferably pinned) transition arrays streamed in chunks of the workspace's max_lines."""
     arr, _ = _conds(cond)
     L = load()
-    broad = profile.kind in ("lorentz", "voigt", "binned_lorentz", "binned_voigt")
+    broad = profile.kind in BROADENED
     a32 = int(A.dtype == torch.float32)
     nb = L.pxc_stream_buffer_bytes(ws.cap.max_lines, a32, int(broad))
     if bufs is None:

@@ -218,14 +218,25 @@ __device__ __noinline__ float w4_core_re(float x, float y) {
   return w4_reg4_re(x, y);
 }
 
+// Region-I (far-wing) Voigt term K (u + 1) / (u^2 + e), u = x^2 + y^2 - 1/2, in the form
+// K (1 + 1/u) / (u + e/u), which stays finite for any representable u (u^2 would overflow FP32
+// beyond |x| ~ 4e9); u >= 200 wherever region I applies.  The fast path uses the direct form on
+// constants rescaled per warp instead (scale_for_pairs).
+__device__ __forceinline__ float region_one(float u, float K, float e) {
+  const float r = frcp(u);
+  return K * (1.f + r) * frcp(fmaf(e, r, u));
+}
+// LineC::masks bit set when a line's region-I terms in a warp need region_one (|x| or y >= 1e9);
+// otherwise the direct K (u + 1) / (u^2 + e), one reciprocal, is used.
+constexpr int kWideRange = 8;
+__device__ __forceinline__ float region_one_or_direct(float u, float K, float e, int masks) {
+  return (masks & kWideRange) ? region_one(u, K, e) : fmaf(u, K, K) * frcp(fmaf(u, u, e));
+}
+
 // Real part of W4 in every region (used by the general path).
 __device__ __forceinline__ float w4_re(float x, float y) {
   const float ax = fabsf(x), s = ax + y;
-  if (s >= 15.f) {
-    float x2 = x * x, y2 = y * y, A = 0.5f + y2;
-    float den = fmaf(x2, x2 + (2.f * y2 - 1.f), A * A);
-    return kInvSqrtPi * y * (A + x2) * frcp(den);
-  }
+  if (s >= 15.f) return region_one(fmaf(x, x, fmaf(y, y, -0.5f)), kInvSqrtPi * y, 2.f * y * y);
   return w4_core_re(x, y);
 }
 
@@ -249,12 +260,56 @@ struct __align__(16) LineC {
   float cen;                   // the centre (grid steps from the segment start)
 };
 
-// Smallest Doppler HWHM used (cm^-1).  Keeps the scaled FP32 arithmetic finite for lines with
-// nu below ~0.05 cm^-1, whose true alpha is far below both the grid step and gamma: the
-// sampled profile changes by less than (alpha/gamma)^2 off the line centre.
-constexpr float kAlphaMin = 8.4e-8f;
+// Smallest Doppler HWHM used by the sampled Gaussian and Voigt kinds (cm^-1): 1/alpha^2 stays a
+// normal FP32 number (the far-wing terms away from the fast path use the overflow-free form of
+// region_one above, so a grid step of up to ~1e13 Doppler widths is fine).  Only lines with nu below
+// ~3e-10 cm^-1 are floored.
+constexpr float kAlphaMin = 1e-15f;
+// The floor of the binned and pseudo-Voigt kinds and of the adjoint, whose bin-mass, common-width
+// and derivative arithmetic is kept finite by it: lines with nu below ~0.05 cm^-1, whose true
+// alpha is far below both the grid step and gamma (the sampled profile changes by less than
+// (alpha/gamma)^2 off the line centre).
+constexpr float kAlphaMinWide = 8.4e-8f;
+
 // Smallest Lorentz HWHM used (cm^-1): gamma^2 stays a normal FP32 number.
 constexpr float kGammaMin = 1e-15f;
+
+// Pseudo-Voigt profiles (Table profile: Thompson, Olivero, Liu-Lin): a Lorentzian and a Gaussian
+// of one common full width G, weights wL and wG, from the Doppler and Lorentz HWHMs alpha, gamma
+// (full widths fG = 2 alpha, fL = 2 gamma):
+//   Thompson (Thompson, Cox, Hastings 1987): G^5 = fG^5 + 2.69269 fG^4 fL + 2.42843 fG^3 fL^2
+//     + 4.47163 fG^2 fL^3 + 0.07842 fG fL^4 + fL^5, wL = 1.36603 r - 0.47719 r^2 + 0.11116 r^3,
+//     r = fL / G, wG = 1 - wL (the fifth power is taken of the widths over the larger one, so no
+//     FP32 over- or underflow);
+//   Olivero (Olivero, Longbothum 1977): G = 0.5346 fL + sqrt(0.2166 fL^2 + fG^2), the same mixing;
+//   Liu-Lin (Liu, Lin et al. 2001): d = (fL - fG)/(fL + fG), G = (fL + fG)(1 - 0.18121 (1 - d^2)
+//     - (0.023665 e^{0.6 d} + 0.00418 e^{-1.9 d}) sin(pi d)), wL = 0.68188 + 0.61293 d - 0.18384 d^2
+//     - 0.11568 d^3, wG = 0.32460 - 0.61825 d + 0.17681 d^2 + 0.12109 d^3.
+template <int KIND>
+__device__ __forceinline__ void pv_params(float alpha, float gamma, float* G, float* wl, float* wg) {
+  const float fG = 2.f * alpha, fL = 2.f * gamma;
+  if (KIND == PXC_PV_LIULIN) {
+    const float d = (fL - fG) * frcp(fL + fG);
+    *G = (fL + fG) * (1.f - 0.18121f * fmaf(-d, d, 1.f) -
+                      (0.023665f * __expf(0.6f * d) + 0.00418f * __expf(-1.9f * d)) * sinpif(d));
+    *wl = fmaf(fmaf(fmaf(-0.11568f, d, -0.18384f), d, 0.61293f), d, 0.68188f);
+    *wg = fmaf(fmaf(fmaf(0.12109f, d, 0.17681f), d, -0.61825f), d, 0.32460f);
+    return;
+  }
+  if (KIND == PXC_PV_THOMPSON) {
+    const float u = fmaxf(fG, fL), iu = frcp(u);
+    const float g = fG * iu, l = fL * iu;
+    const float g2 = g * g, l2 = l * l;
+    const float s5 = g2 * g2 * g + 2.69269f * g2 * g2 * l + 2.42843f * g2 * g * l2 + 4.47163f * g2 * l2 * l +
+                     0.07842f * g * l2 * l2 + l2 * l2 * l;
+    *G = u * exp2f(0.2f * __log2f(s5));
+  } else {
+    *G = fmaf(0.5346f, fL, sqrtf(fmaf(0.2166f * fL, fL, fG * fG)));
+  }
+  const float r = fL * frcp(*G);
+  *wl = r * fmaf(fmaf(0.11116f, r, -0.47719f), r, 1.36603f);
+  *wg = 1.f - *wl;
+}
 
 // Per-line constants for the warp owning points [wbase, wbase + 32 PTS) of the segment.  All
 // FP32: the centre wavenumber that scales the Doppler width is rebuilt from the grid index and
@@ -272,7 +327,7 @@ __device__ __forceinline__ void line_constants(const int4 p4, const float2 pr, c
   c.hi = (int)(hi > SEG - 1 ? SEG - 1 : hi);
   const float cen = c.pf + f;  // line centre in grid steps from the segment start
   float reach = 0.f;           // half-width (grid steps) of the zone needing the general path
-  if (KIND >= PXC_BINNED_GAUSS_DOPPLER) {
+  if (is_binned(KIND)) {
     // Binned profiles: t = bin-centre offset in the kind's scaled unit; the bin is [t - h, t + h]
     // with h = step / 2 (see eval_binned).
     constexpr int BASE = KIND & 3;
@@ -284,7 +339,7 @@ __device__ __forceinline__ void line_constants(const int4 p4, const float2 pr, c
       c.y = g;
     } else {
       const float nu = fmaf((float)ic + f, dnu_f, nu_min_f);
-      const float alpha = fmaxf(BASE == PXC_GAUSS_HWHM ? cd.hwhm : cd.alpha_coef * nu, kAlphaMin);
+      const float alpha = fmaxf(BASE == PXC_GAUSS_HWHM ? cd.hwhm : cd.alpha_coef * nu, kAlphaMinWide);
       const float cc = kSqrtLn2 * frcp(alpha);  // 1 / (s sqrt 2)
       c.step = dnu_f * cc;
       if (BASE == PXC_VOIGT) {
@@ -310,7 +365,24 @@ __device__ __forceinline__ void line_constants(const int4 p4, const float2 pr, c
     c.masks = (valid && is != 0.f && c.lo <= c.hi) ? 1 : 0;
     return;
   }
-  if (KIND == PXC_LORENTZ) {
+  if (is_pseudo_voigt(KIND)) {
+    // t = (nu_i - nu_l) / h, h = G / 2: f = wL / (pi h (1 + t^2)) + wG sqrt(ln2 / pi) / h 2^(-t^2)
+    const float nu = fmaf((float)ic + f, dnu_f, nu_min_f);
+    const float alpha = fmaxf(cd.alpha_coef * nu, kAlphaMinWide);
+    const float g = pr.x * exp2f(pr.y * cd.log2_tratio) * cd.P_f;
+    float G, wl, wg;
+    pv_params<KIND>(alpha, g, &G, &wl, &wg);
+    const float ih = 2.f * frcp(G);
+    c.step = dnu_f * ih;
+    c.nfs = -f * c.step;
+    c.K = is * wl * kInvPi * ih;
+    c.KA = is * wg * (kSqrtLn2 * kInvSqrtPi) * ih;
+    c.Kc = c.K;
+    c.B1 = 0.f; c.y = 0.f;
+    c.a = (float)wbase - c.pf;
+    c.b = c.step;
+    c.d = c.nfs;
+  } else if (KIND == PXC_LORENTZ) {
     const float g = fmaxf(pr.x * exp2f(pr.y * cd.log2_tratio) * cd.P_f, kGammaMin);
     c.step = dnu_f;
     c.nfs = -f * dnu_f;
@@ -374,7 +446,7 @@ template <int KIND, int WPTS>
 __device__ __forceinline__ int line_class(const LineC& c, int a) {
   const int b = a + WPTS - 1;
   if (!c.masks || c.hi < a || c.lo > b) return 0;
-  if (KIND >= PXC_BINNED_GAUSS_DOPPLER) return 2;  // binned kinds: one masked path (eval_binned)
+  if (is_binned(KIND)) return 2;  // binned kinds: one masked path (eval_binned)
   bool far = true;
   if (KIND == PXC_VOIGT) {
     const float dmin = fmaxf(0.f, fmaxf(c.cen - (float)b, (float)a - c.cen));
@@ -390,29 +462,63 @@ __device__ __forceinline__ int line_class(const LineC& c, int a) {
 }
 
 
+// Far-wing Voigt lines evaluated in pairs share one reciprocal: n1/d1 + n2/d2 = (n1 d2 + n2 d1) /
+// (d1 d2).  To keep d1 d2 inside the FP32 range, each fast line's constants are rescaled for its
+// warp by sigma = 2^-e, e the exponent of x_ref = max(min |x| over the warp's points, y): with
+// x' = sigma x every term of K (v + 1) / (v^2 + e) scales exactly (v' = sigma^2 v, the numerator by
+// sigma^2, the denominator by sigma^4), so the value is unchanged and the scaled denominators lie
+// in [~1, 2^52] when max |x| <= 2^12 x_ref.  Returns false (the line then takes the masked
+// single-line path) when the warp spans a wider range of |x| than that.
+template <int WPTS>
+__device__ __forceinline__ bool scale_for_pairs(LineC& c, int wbase) {
+  const float wlo = (float)wbase, whi = (float)(wbase + WPTS - 1);
+  const float dmin = fmaxf(0.f, fmaxf(c.cen - whi, wlo - c.cen));
+  const float dmax = fmaxf(fabsf(c.cen - wlo), fabsf(c.cen - whi));
+  const float xref = fmaxf(dmin * c.step, c.y);
+  if (!(xref > 0.f) || !(dmax * c.step <= 4096.f * xref)) return false;
+  const int ex = (__float_as_int(xref) >> 23) & 0xff;  // xref = m 2^(ex - 127), 1 <= m < 2
+  const float sg = __int_as_float((254 - ex) << 23);   // 2^(127 - ex)
+  const float sg2 = sg * sg;
+  c.a *= sg;
+  c.b *= sg;
+  c.B1 *= sg2;
+  c.d *= sg2 * sg2;
+  c.KA = c.K * (sg2 * sg2);
+  c.K *= sg2;
+  return true;
+}
+
 // Branch-free evaluation of one line at the lane's PTS points (fast class); lk[k] = lane + 32 k.
 template <int KIND, int PTS>
 __device__ __forceinline__ void eval_fast(const LineC& c, const float* lk, float* acc) {
-  if (KIND >= PXC_BINNED_GAUSS_DOPPLER) return;  // binned lines are never in the fast class
+  if (is_binned(KIND)) return;  // binned lines are never in the fast class
   const float4 f0 = *reinterpret_cast<const float4*>(&c.a);  // a, b, B1, d
   const float K = c.K;
   if (KIND == PXC_VOIGT) {
     // far wing, W4 region I: K (v + 1) / (v^2 + e), v = x^2 + c1 (five FP32 FMAs and one MUFU
     // reciprocal per point); no point of this warp is near the centre, so x = x(lane 0) + m step
     // keeps full relative accuracy
+    const float KA = c.KA;  // K sigma^4, the rescaled numerator's constant term
 #pragma unroll
     for (int k = 0; k < PTS; ++k) {
       const float x = fmaf(lk[k], f0.y, f0.x);
       const float v = fmaf(x, x, f0.z);
-      acc[k] = fmaf(fmaf(v, K, K), frcp(fmaf(v, v, f0.w)), acc[k]);
+      acc[k] = fmaf(fmaf(v, K, KA), frcp(fmaf(v, v, f0.w)), acc[k]);
     }
   } else {
     // the line centre may lie among these points: x from the exact integer offset
+    const float KG = c.KA;
 #pragma unroll
     for (int k = 0; k < PTS; ++k) {
       const float x = fmaf(lk[k] + f0.x, f0.y, f0.w);
-      if (KIND == PXC_LORENTZ) acc[k] = fmaf(K, frcp(fmaf(x, x, f0.z)), acc[k]);
-      else acc[k] = fmaf(K, fex2(-(x * x)), acc[k]);
+      if (is_pseudo_voigt(KIND)) {
+        const float x2 = x * x;
+        acc[k] = fmaf(K, frcp(x2 + 1.f), fmaf(KG, fex2(-x2), acc[k]));
+      } else if (KIND == PXC_LORENTZ) {
+        acc[k] = fmaf(K, frcp(fmaf(x, x, f0.z)), acc[k]);
+      } else {
+        acc[k] = fmaf(K, fex2(-(x * x)), acc[k]);
+      }
     }
   }
 }
@@ -420,7 +526,7 @@ __device__ __forceinline__ void eval_fast(const LineC& c, const float* lk, float
 // Two lines at once (more independent work per point, half the loop overhead).
 template <int KIND, int PTS>
 __device__ __forceinline__ void eval_fast2(const LineC& c, const LineC& e, const float* lk, float* acc) {
-  if (KIND >= PXC_BINNED_GAUSS_DOPPLER) return;
+  if (is_binned(KIND)) return;
   if (KIND == PXC_VOIGT) {
     const float4 a0 = *reinterpret_cast<const float4*>(&c.a), a1 = *reinterpret_cast<const float4*>(&c.K);
     const float4 b0 = *reinterpret_cast<const float4*>(&e.a), b1 = *reinterpret_cast<const float4*>(&e.K);
@@ -428,8 +534,10 @@ __device__ __forceinline__ void eval_fast2(const LineC& c, const LineC& e, const
     for (int k = 0; k < PTS; ++k) {
       const float x = fmaf(lk[k], a0.y, a0.x), y = fmaf(lk[k], b0.y, b0.x);
       const float u = fmaf(x, x, a0.z), v = fmaf(y, y, b0.z);
-      const float ra = frcp(fmaf(u, u, a0.w)), rb = frcp(fmaf(v, v, b0.w));
-      acc[k] = fmaf(fmaf(u, a1.x, a1.x), ra, fmaf(fmaf(v, b1.x, b1.x), rb, acc[k]));
+      const float du = fmaf(u, u, a0.w), dv = fmaf(v, v, b0.w);
+      const float nu = fmaf(u, a1.x, a1.y), nv = fmaf(v, b1.x, b1.y);
+      // n_u / d_u + n_v / d_v with one reciprocal (six FP32 operations and half a MUFU per point)
+      acc[k] = fmaf(fmaf(nv, du, nu * dv), frcp(du * dv), acc[k]);
     }
   } else {
     eval_fast<KIND, PTS>(c, lk, acc);
@@ -489,7 +597,7 @@ __device__ __forceinline__ void eval_binned(const LineC& c, int wbase, int lane,
 // Far-wing formula with a lane mask (the window ends among this warp's points).
 template <int KIND, int PTS>
 __device__ __forceinline__ void eval_fastmask(const LineC& c, int wbase, int lane, float* acc) {
-  if (KIND >= PXC_BINNED_GAUSS_DOPPLER) {
+  if (is_binned(KIND)) {
     eval_binned<KIND, PTS>(c, wbase, lane, acc);
     return;
   }
@@ -501,15 +609,20 @@ __device__ __forceinline__ void eval_fastmask(const LineC& c, int wbase, int lan
 #pragma unroll
     for (int k = 0; k < PTS; ++k) {
       const float x = fmaf((float)k, s32, x0);
-      const float u = fmaf(x, x, c.B1);
-      const float v = fmaf(u, c.K, c.K) * frcp(fmaf(u, u, c.d));
+      const float v = region_one_or_direct(fmaf(x, x, c.B1), c.K, c.d, c.masks);
       acc[k] += (unsigned)(rel0 + 32 * k) <= span ? v : 0.f;
     }
   } else {
 #pragma unroll
     for (int k = 0; k < PTS; ++k) {
       const float x = fmaf((float)(wbase + lane + 32 * k) - c.pf, c.step, c.nfs);
-      const float v = KIND == PXC_LORENTZ ? c.K * frcp(fmaf(x, x, c.B1)) : c.K * fex2(-(x * x));
+      float v;
+      if (is_pseudo_voigt(KIND)) {
+        const float x2 = x * x;
+        v = fmaf(c.K, frcp(x2 + 1.f), c.KA * fex2(-x2));
+      } else {
+        v = KIND == PXC_LORENTZ ? c.K * frcp(fmaf(x, x, c.B1)) : c.K * fex2(-(x * x));
+      }
       acc[k] += (unsigned)(rel0 + 32 * k) <= span ? v : 0.f;
     }
   }
@@ -535,9 +648,8 @@ __device__ __forceinline__ RegionII region2(float y) {
   return r;
 }
 
-// Warps near the centre whose points all have |x| + y >= 5.5: the region II rational at every
-// point (W4's two-level continued fraction, at least as accurate as region I wherever that one
-// applies), window edges masked, no per-point branches.
+// Warps near the centre whose points all have |x| + y >= 5.5: the region II rational (W4's
+// two-level continued fraction) where |x| + y < 15 and region I beyond, window edges masked.
 template <int KIND, int PTS>
 __device__ __forceinline__ void eval_mid(const LineC& c, int wbase, int lane, float* acc) {
   if (KIND != PXC_VOIGT) return;
@@ -551,25 +663,36 @@ __device__ __forceinline__ void eval_mid(const LineC& c, int wbase, int lane, fl
   for (int k = 0; k < PTS; ++k) {
     const float x = fmaf((float)k, s32, x0);
     const float X = x * x;
-    const float N = fmaf(fmaf(fmaf(r.n3, X, r.n2), X, r.n1), X, r.n0);
-    const float D = fmaf(fmaf(fmaf(X + r.d3, X, r.d2), X, r.d1), X, r.d0);
-    acc[k] += (unsigned)(rel0 + 32 * k) <= span ? Ky * N * frcp(D) : 0.f;
+    float v;
+    if (fabsf(x) + c.y >= 15.f) {  // region I: the quartic below would overflow FP32 for very large x
+      v = region_one_or_direct(X + c.B1, c.K, c.d, c.masks);
+    } else {
+      const float N = fmaf(fmaf(fmaf(r.n3, X, r.n2), X, r.n1), X, r.n0);
+      const float D = fmaf(fmaf(fmaf(X + r.d3, X, r.d2), X, r.d1), X, r.d0);
+      v = Ky * N * frcp(D);
+    }
+    acc[k] += (unsigned)(rel0 + 32 * k) <= span ? v : 0.f;
   }
 }
 
-// Warps near the line core (Voigt), some point in W4 regions III/IV: blocks of 32 points far
-// from the centre keep the region-I formula; elsewhere each point takes its W4 region.  Region
-// II (5.5 <= |x|+y < 15) is the real rational Re w = y N(X) / D(X) in X = x^2 (N cubic, D monic
-// quartic, coefficients from Y = y^2 once per line and warp; Humlicek's constants satisfy
-// a = 2.5 b, which gives the factored forms of region2); only |x|+y < 5.5 needs the complex
-// regions III/IV.  (Gathering the region III/IV points of a warp to evaluate them on full warps
-// measured slower than this divergent form.)
+// Warps near the line core (Voigt), some point with |x| + y < 5.5.  Points with |x| + y >= 15 take
+// region I, points with 5.5 <= |x| + y < 15 W4's region-II formula, the real rational
+// Re w = y N(X) / D(X) in X = x^2 (N cubic, D monic quartic, coefficients from Y = y^2 once per line
+// and warp; Humlicek's constants satisfy a = 2.5 b, which gives the factored forms of region2).
+// Points with |x| + y < 5.5 take one formula per line where one
+// suffices: for y <= 0.4 the region-IV form e^u - t P(u) / Q(u) over the whole disc (measured in
+// FP32 against scipy's wofz: <= 4.8e-5 relative wherever Re w > 1e-6 of its peak, below W4's own
+// region III/IV split, 9.1e-5), for y >= 0.9 the region-III rational (<= 3.8e-5; that whole disc
+// is region III), and W4's region III/IV test per point in between.  A block then follows at most
+// three paths instead of four.  Blocks of 32 points whose nearest point is beyond the
+// region-I reach keep the region-I formula (a uniform branch).
 template <int KIND, int PTS>
 __device__ __forceinline__ void eval_slow(const LineC& c, int wbase, int lane, const float* lk, float* acc) {
-  if (KIND >= PXC_BINNED_GAUSS_DOPPLER) return;  // binned lines are never in the core class
+  if (is_binned(KIND)) return;  // binned lines are never in the core class
   const unsigned span = (unsigned)(c.hi - c.lo);
   const RegionII r = region2(c.y);
   const float Ky = c.Kc * c.y;
+  const int core = c.y <= 0.4f ? 4 : (c.y >= 0.9f ? 3 : 0);
 #pragma unroll
   for (int k = 0; k < PTS; ++k) {
     const int b0 = wbase + 32 * k;
@@ -577,25 +700,27 @@ __device__ __forceinline__ void eval_slow(const LineC& c, int wbase, int lane, c
     const int li = b0 + lane;
     const bool in = (unsigned)(li - c.lo) <= span;
     const float dmin = fmaxf(0.f, fmaxf(c.cen - (float)(b0 + 31), (float)b0 - c.cen));
-    if (PTS >= 8 && dmin > c.reach) {
-      // the whole block is in region I (uniform branch): the fast-path formula (measured to pay
-      // off for wide warps only; narrow ones rarely have such blocks among their slow lines)
+    if (dmin > c.reach) {
+      // the whole block is in region I (uniform branch): the fast-path formula
       const float x = fmaf(lk[k], c.b, c.a);
-      const float u = fmaf(x, x, c.B1);
-      const float v = fmaf(u, c.K, c.K) * frcp(fmaf(u, u, c.d));
-      acc[k] += in ? v : 0.f;
+      acc[k] += in ? region_one_or_direct(fmaf(x, x, c.B1), c.K, c.d, c.masks) : 0.f;
       continue;
     }
     const float x = fmaf((float)li - c.pf, c.step, c.nfs);
+    const float sx = fabsf(x) + c.y;
     float v;
-    const float x2 = x * x;
-    if (fabsf(x) + c.y >= 15.f) {
-      const float u = fmaf(x, x, c.B1);
-      v = fmaf(u, c.K, c.K) * frcp(fmaf(u, u, c.d));
-    } else if (fabsf(x) + c.y >= 5.5f) {
-      const float N = fmaf(fmaf(fmaf(r.n3, x2, r.n2), x2, r.n1), x2, r.n0);
-      const float D = fmaf(fmaf(fmaf(x2 + r.d3, x2, r.d2), x2, r.d1), x2, r.d0);
+    if (sx >= 15.f) {
+      // region I (the region-II quartic in x^2 would leave the FP32 range for very large x)
+      v = region_one_or_direct(fmaf(x, x, c.B1), c.K, c.d, c.masks);
+    } else if (sx >= 5.5f) {
+      const float X = x * x;
+      const float N = fmaf(fmaf(fmaf(r.n3, X, r.n2), X, r.n1), X, r.n0);
+      const float D = fmaf(fmaf(fmaf(X + r.d3, X, r.d2), X, r.d1), X, r.d0);
       v = Ky * N * frcp(D);
+    } else if (core == 4) {
+      v = c.Kc * w4_reg4_re(x, c.y);
+    } else if (core == 3) {
+      v = c.Kc * w4_reg3_re(x, c.y);
     } else {
       v = c.Kc * w4_core_re(x, c.y);
     }
@@ -698,10 +823,17 @@ __global__ void __launch_bounds__(THREADS, MINB) k_profile(const ProfP p) {
         const float is = reinterpret_cast<const float*>(src + SL * 24)[j];
         LineC c;
         line_constants<KIND, SEG>(p4, pr, is, cd, i0, wbase, dnu_f, nu_min_f, J >= item.begin && J < item.end, c);
-        const int cls = line_class<KIND, WPTS>(c, wbase);
+        int cls = line_class<KIND, WPTS>(c, wbase);
+        if (KIND == PXC_VOIGT && cls == 1 && !scale_for_pairs<WPTS>(c, wbase)) cls = 2;
         c.masks = cls;
+        // unscaled region-I terms of this line and warp: the direct form unless |x| or y reaches
+        // 1e9 somewhere in the warp (then u^2 could leave the FP32 range)
+        if (KIND == PXC_VOIGT && cls >= 2) {
+          const float dmax = fmaxf(fabsf(c.cen - (float)wbase), fabsf(c.cen - (float)(wbase + WPTS - 1)));
+          if (dmax * c.step > 1e9f || c.y > 1e9f) c.masks |= kWideRange;
+        }
         const unsigned bf = __ballot_sync(0xffffffffu, cls == 1);
-        const unsigned bo = __ballot_sync(0xffffffffu, cls >= 2);
+        const unsigned bo = __ballot_sync(0xffffffffu, cls >= 2);  // cls: the class before the range flag
         if (cls == 1) my[nf + __popc(bf & lt)] = c;
         if (cls >= 2) my[SL - 1 - (no + __popc(bo & lt))] = c;
         nf += __popc(bf);
@@ -728,8 +860,9 @@ __global__ void __launch_bounds__(THREADS, MINB) k_profile(const ProfP p) {
       if (i < nf) eval_fast<KIND, PTS>(my[i], lk, acc);
       for (int q = SL - 1; q >= SL - no; --q) {
         const LineC& c = my[q];
-        if (c.masks == 2) eval_fastmask<KIND, PTS>(c, wbase, lane, acc);
-        else if (c.masks == 4) eval_mid<KIND, PTS>(c, wbase, lane, acc);
+        const int cls = c.masks & 7;
+        if (cls == 2) eval_fastmask<KIND, PTS>(c, wbase, lane, acc);
+        else if (cls == 4) eval_mid<KIND, PTS>(c, wbase, lane, acc);
         else eval_slow<KIND, PTS>(c, wbase, lane, lk, acc);
       }
 #pragma unroll
@@ -763,7 +896,9 @@ __global__ void __launch_bounds__(THREADS, MINB) k_profile(const ProfP p) {
 }
 
 // Compiled tile configurations: {threads, points per lane, lines per stage, min CTAs per SM}.
-// Segment widths 128, 256, 1024 and 2048 points.
+// Segment widths 128, 256, 1024 and 2048 points.  (One-warp tiles of 256 and 512 points, with
+// fewer line-warp constant builds per evaluation, measured slower than tile 0 on the 1e9-line
+// list: 12.4 and 17.9 against 11.4 ms per 1e8-line call.)
 #define PXC_TILES(X) X(0, 32, 4, 64, 32) X(1, 64, 4, 64, 16) X(2, 128, 8, 64, 6) X(3, 128, 16, 128, 4)
 
 int tile_seg(int tile) {
@@ -803,6 +938,9 @@ int profile_occupancy(int kind, int tile) {
     case PXC_BINNED_GAUSS_HWHM: return occupancy_kind<PXC_BINNED_GAUSS_HWHM>(tile);
     case PXC_BINNED_LORENTZ: return occupancy_kind<PXC_BINNED_LORENTZ>(tile);
     case PXC_BINNED_VOIGT: return occupancy_kind<PXC_BINNED_VOIGT>(tile);
+    case PXC_PV_THOMPSON: return occupancy_kind<PXC_PV_THOMPSON>(tile);
+    case PXC_PV_OLIVERO: return occupancy_kind<PXC_PV_OLIVERO>(tile);
+    case PXC_PV_LIULIN: return occupancy_kind<PXC_PV_LIULIN>(tile);
     default: return occupancy_kind<PXC_VOIGT>(tile);
   }
 }
@@ -824,7 +962,134 @@ void launch_profile(const ProfP& p, int tile, int grid_ctas, cudaStream_t s) {
     case PXC_BINNED_GAUSS_HWHM: launch_kind<PXC_BINNED_GAUSS_HWHM>(p, tile, grid_ctas, s); break;
     case PXC_BINNED_LORENTZ: launch_kind<PXC_BINNED_LORENTZ>(p, tile, grid_ctas, s); break;
     case PXC_BINNED_VOIGT: launch_kind<PXC_BINNED_VOIGT>(p, tile, grid_ctas, s); break;
+    case PXC_PV_THOMPSON: launch_kind<PXC_PV_THOMPSON>(p, tile, grid_ctas, s); break;
+    case PXC_PV_OLIVERO: launch_kind<PXC_PV_OLIVERO>(p, tile, grid_ctas, s); break;
+    case PXC_PV_LIULIN: launch_kind<PXC_PV_LIULIN>(p, tile, grid_ctas, s); break;
     default: launch_kind<PXC_VOIGT>(p, tile, grid_ctas, s); break;
+  }
+  note_launches(1);
+}
+
+// ------------------------------------------------------------------ wavelength grids
+// Eq. (xsec) sampled on a wavelength grid (Sec. 2.4.3): lambda_i = lambda_min + i dlambda,
+// nu_i = U / lambda_i.  Each line's position in grid steps is (U/nu_l - lambda_min)/dlambda =
+// ic + f (FP64 in the preparation pass), so the offset from the line centre is
+//   nu_i - nu_l = U (lambda_l - lambda_i) / (lambda_i lambda_l) = ((ic - i) + f) (U dlambda / lambda_l) / lambda_i
+// with the integer difference exact in FP32 and no cancellation between nearly equal wavenumbers.
+// A CTA of kSegWl threads takes one work item (a segment and its line range) at a time, thread j
+// owning point i0 + j; the lines' constants are built once per staged line (thread q builds line q
+// of the stage) and every thread adds the lines whose window holds its point.  The Voigt kind
+// evaluates Humlicek's W4 in every region; the pseudo-Voigts a Lorentzian and a Gaussian.
+struct LineWl {
+  int ic, lo, hi, ok;
+  float f, kd;     // position fraction; U dlambda / lambda_l (cm^-1 per grid step at lambda_i = lambda_l)
+  float s, y;      // Gauss/Voigt: 1/(s sqrt2) = sqrt(ln2)/alpha and y; Lorentz: gamma; pseudo-Voigt: 1/h
+  float K, K2;     // amplitudes (pseudo-Voigt: Lorentzian and Gaussian parts)
+};
+
+template <int KIND>
+__device__ __forceinline__ LineWl line_constants_wl(const int4 p4, const float2 pr, float is, const CondDev& cd,
+                                                    const ProfP& p, bool valid) {
+  LineWl c;
+  c.ic = p4.x;
+  c.f = __int_as_float(p4.y);
+  c.lo = p4.z;
+  c.hi = p4.w;
+  const double lam_l = p.nu_min + ((double)c.ic + (double)c.f) * p.dnu;
+  const float nu = (float)(p.wl_unit / lam_l);
+  c.kd = (float)(p.wl_unit * p.dnu / lam_l);
+  const float g = pr.x * exp2f(pr.y * cd.log2_tratio) * cd.P_f;
+  c.ok = valid && is != 0.f && c.lo <= c.hi;
+  if (KIND == PXC_LORENTZ) {
+    const float gm = fmaxf(g, kGammaMin);
+    c.s = gm;
+    c.y = gm * gm;
+    c.K = is * gm * kInvPi;
+    c.K2 = 0.f;
+    return c;
+  }
+  const float alpha = fmaxf(KIND == PXC_GAUSS_HWHM ? cd.hwhm : cd.alpha_coef * nu,
+                            is_pseudo_voigt(KIND) ? kAlphaMinWide : kAlphaMin);
+  if (is_pseudo_voigt(KIND)) {
+    float G, wl, wg;
+    pv_params<KIND>(alpha, g, &G, &wl, &wg);
+    const float ih = 2.f / G;
+    c.s = ih;
+    c.y = 0.f;
+    c.K = is * wl * kInvPi * ih;
+    c.K2 = is * wg * (kSqrtLn2 * kInvSqrtPi) * ih;
+    return c;
+  }
+  const float cc = kSqrtLn2 / alpha;
+  c.s = cc;
+  c.y = KIND == PXC_VOIGT ? g * cc : 0.f;
+  c.K = is * cc * kInvSqrtPi;
+  c.K2 = 0.f;
+  return c;
+}
+
+template <int KIND>
+__device__ __forceinline__ float eval_wl(const LineWl& c, float dnu_pt) {
+  if (KIND == PXC_LORENTZ) return c.K * frcp(fmaf(dnu_pt, dnu_pt, c.y));
+  if (is_pseudo_voigt(KIND)) {
+    const float t = dnu_pt * c.s, t2 = t * t;
+    return fmaf(c.K, frcp(t2 + 1.f), c.K2 * fex2(-t2));
+  }
+  const float x = dnu_pt * c.s;
+  if (KIND == PXC_VOIGT) return c.K * w4_re(x, c.y);
+  return c.K * __expf(-x * x);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kSegWl) k_profile_wl(const ProfP p) {
+  __shared__ LineWl sl[kSegWl];
+  const unsigned long long n_items = *p.n_items;
+  for (unsigned long long it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const Item item = p.items[it];
+    const CondDev cd = p.cond[item.cond];
+    const float* Is = p.Is + (int64_t)cd.slot * p.is_stride;
+    const int64_t gi = (int64_t)item.seg * kSegWl + threadIdx.x;
+    const float inv_lam = (float)(1.0 / (p.nu_min + (double)gi * p.dnu));
+    float sum = 0.f;
+    for (int j0 = item.begin; j0 < item.end; j0 += kSegWl) {
+      const int n = min(kSegWl, item.end - j0);
+      __syncthreads();  // the previous stage's constants are no longer read
+      if ((int)threadIdx.x < n) {
+        const int j = j0 + (int)threadIdx.x;
+        sl[threadIdx.x] = line_constants_wl<KIND>(p.pos[j], p.par[j], Is[j], cd, p, true);
+      }
+      __syncthreads();
+      float stage = 0.f;
+      for (int q = 0; q < n; ++q) {
+        const LineWl& c = sl[q];
+        if (!c.ok || gi < c.lo || gi > c.hi) continue;
+        const float dnu_pt = ((float)(c.ic - (int)gi) + c.f) * c.kd * inv_lam;
+        stage += eval_wl<KIND>(c, dnu_pt);
+      }
+      sum += stage;
+    }
+    if (gi < p.n_grid) {
+      float* o = p.sigma + (int64_t)item.cond * p.n_grid + gi;
+      if (item.slot < 0) {
+        if (p.accumulate) { if (item.end > item.begin) *o += sum; } else *o = sum;
+      } else {
+        p.partial[(int64_t)item.slot * kSegWl + threadIdx.x] = sum;
+      }
+    }
+  }
+}
+
+void launch_profile_wl(const ProfP& p, int64_t max_items, cudaStream_t s) {
+  int64_t blocks = max_items < 148 * 16 ? max_items : 148 * 16;
+  if (blocks < 1) blocks = 1;
+  switch (p.kind) {
+    case PXC_GAUSS_DOPPLER: k_profile_wl<PXC_GAUSS_DOPPLER><<<(unsigned)blocks, kSegWl, 0, s>>>(p); break;
+    case PXC_GAUSS_HWHM: k_profile_wl<PXC_GAUSS_HWHM><<<(unsigned)blocks, kSegWl, 0, s>>>(p); break;
+    case PXC_LORENTZ: k_profile_wl<PXC_LORENTZ><<<(unsigned)blocks, kSegWl, 0, s>>>(p); break;
+    case PXC_PV_THOMPSON: k_profile_wl<PXC_PV_THOMPSON><<<(unsigned)blocks, kSegWl, 0, s>>>(p); break;
+    case PXC_PV_OLIVERO: k_profile_wl<PXC_PV_OLIVERO><<<(unsigned)blocks, kSegWl, 0, s>>>(p); break;
+    case PXC_PV_LIULIN: k_profile_wl<PXC_PV_LIULIN><<<(unsigned)blocks, kSegWl, 0, s>>>(p); break;
+    default: k_profile_wl<PXC_VOIGT><<<(unsigned)blocks, kSegWl, 0, s>>>(p); break;
   }
   note_launches(1);
 }
@@ -851,7 +1116,7 @@ __global__ void __launch_bounds__(256) k_adjoint(const AdjP p) {
     const int ic = p4.x;
     const float f = __int_as_float(p4.y);
     const float nu_f = (float)(p.nu_min + ((double)ic + (double)f) * p.dnu);
-    const float alpha = fmaxf(KIND == PXC_GAUSS_HWHM ? p.cond.hwhm : p.cond.alpha_coef * nu_f, kAlphaMin);
+    const float alpha = fmaxf(KIND == PXC_GAUSS_HWHM ? p.cond.hwhm : p.cond.alpha_coef * nu_f, kAlphaMinWide);
     const float gfac = exp2f(pr.y * p.cond.log2_tratio) * p.cond.P_f;   // dgamma/dgamma_ref
     const float gam = KIND == PXC_LORENTZ ? fmaxf(pr.x * gfac, kGammaMin) : KIND == PXC_VOIGT ? pr.x * gfac : 0.f;
     const float cc = kSqrtLn2 / alpha;

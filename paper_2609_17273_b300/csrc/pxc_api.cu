@@ -92,7 +92,7 @@ Layout make_layout(const pxc_capacity& c) {
   L.kexp = take((size_t)L.max_slots * 2 * 4);
   L.maxbits = take((size_t)L.max_slots * 8);
   L.params = take(4096);
-  L.code = take((size_t)std::max<int64_t>(c.max_states, 1) * sizeof(code_t));
+  L.code = take(code_bytes(std::max<int64_t>(c.max_states, 1)));
   L.qwords = take(kQuantWords * 8 + sizeof(QuantHdr));
   L.total = o;
   return L;
@@ -127,6 +127,9 @@ pxc_status check_cond(const pxc_condition& c, bool need_vib, const pxc_states* s
 pxc_status check_grid(const pxc_grid* g, double cut) {
   if (!g || !(g->dnu > 0.0) || g->n < 1 || !std::isfinite(g->nu_min) || !std::isfinite(g->dnu))
     return fail(PXC_ERR_ARG, "grid: dnu must be > 0 and n >= 1");
+  if (!(g->wl_unit >= 0.0) || !std::isfinite(g->wl_unit))
+    return fail(PXC_ERR_ARG, "grid: wl_unit must be 0 (wavenumbers) or > 0 (wavelengths)");
+  if (g->wl_unit > 0.0 && !(g->nu_min > 0.0)) return fail(PXC_ERR_ARG, "grid: wavelengths must be > 0");
   if (!(cut >= 0.0) || !std::isfinite(cut)) return fail(PXC_ERR_ARG, "cutoff must be finite and >= 0");
   if (g->n > (int64_t)INT32_MAX - 2 * kSegMax) return fail(PXC_ERR_ARG, "grid: too many points");
   return PXC_OK;
@@ -145,7 +148,19 @@ double bitsd(uint64_t b) { double d; memcpy(&d, &b, 8); return d; }
 GridP make_gridp(const pxc_grid& g, double cut) {
   GridP gp{};
   gp.nu_min = g.nu_min; gp.dnu = g.dnu; gp.cut = cut; gp.n = g.n;
+  gp.wl_unit = g.wl_unit;
   gp.exact_bounds = 0;
+  const double last = g.nu_min + (double)(g.n - 1) * g.dnu;
+  if (g.wl_unit > 0.0) {
+    // wavelength grid: kept lines have nu within [U/lambda_max - cut, U/lambda_min + cut]
+    // (widened by 1e-6 relative for the rounding of the window arithmetic); windows per line
+    const double a = g.wl_unit / last - cut, b = g.wl_unit / g.nu_min + cut;
+    gp.nu_span_lo = std::max(0.0, a - 1e-6 * std::fabs(a) - 1e-6 * cut);
+    gp.nu_span_hi = b + 1e-6 * std::fabs(b);
+    return gp;
+  }
+  gp.nu_span_lo = std::max(g.nu_min - cut, 0.0);
+  gp.nu_span_hi = last + cut;
   if (!(cut >= 1.5 * g.dnu)) return gp;  // short windows can fall between points: test each line
   const uint64_t LO = 1, HI = dbits(1.7976931348623157e308);
   auto p_lo = [&](uint64_t b) { return win_hi_idx(bitsd(b), cut, g.nu_min, g.dnu) >= 0.0; };
@@ -263,10 +278,14 @@ CondDev make_cond(const pxc_condition& c, const pxc_profile_args& pa, int slot) 
   return cd;
 }
 
+// Width kind of a profile: binned kinds take the widths of their base kind, pseudo-Voigts those of
+// the Voigt kind.
+int width_kind(int kind) { return is_pseudo_voigt(kind) ? PXC_VOIGT : (kind & 3); }
+
 pxc_status check_prof(const pxc_profile_args* pa, const pxc_transitions* tr) {
   if (!pa) return fail(PXC_ERR_ARG, "profile args: null");
-  if (pa->kind < PXC_GAUSS_DOPPLER || pa->kind > PXC_BINNED_VOIGT) return fail(PXC_ERR_ARG, "profile: unknown kind");
-  const int base = pa->kind & 3;  // binned kinds take the widths of their base kind
+  if (pa->kind < PXC_GAUSS_DOPPLER || pa->kind > PXC_PV_LIULIN) return fail(PXC_ERR_ARG, "profile: unknown kind");
+  const int base = width_kind(pa->kind);
   if ((base == PXC_GAUSS_DOPPLER || base == PXC_VOIGT) && !(pa->mass_da > 0.0))
     return fail(PXC_ERR_ARG, "profile: mass must be > 0");
   if (base == PXC_GAUSS_HWHM && !(pa->hwhm > 0.0)) return fail(PXC_ERR_ARG, "profile: hwhm must be > 0");
@@ -312,6 +331,12 @@ BoundP make_bound(pxc_workspace* ws, const pxc_states* st, const pxc_condition& 
   return bp;
 }
 
+// The intensity pass's candidate arrays reuse sort buffers that are free until the kept lines are
+// compacted (sidx0, skey0, skey1) and the radix counts (one count per unit).
+#define CAND_BUFFERS(ws, L)                                                                       \
+  at<uint32_t>(ws, (L).sidx0), at<uint64_t>(ws, (L).skey0), at<uint64_t>(ws, (L).skey1), \
+      at<uint32_t>(ws, (L).rcount)
+
 // Lines -> kept, sorted, prepared (plain single-condition path).  with_gather fills su/sl/sA.
 pxc_status front_plain(pxc_workspace* ws, const pxc_states* st, const pxc_transitions* tr, const pxc_condition& c,
                        const GridP& gp, const pxc_profile_args* pa, double threshold, int32_t* sig_exp, float* sigma,
@@ -325,9 +350,9 @@ pxc_status front_plain(pxc_workspace* ws, const pxc_states* st, const pxc_transi
   tmark(ws, 0, true, s);
   BoundP bp = make_bound(ws, st, c, threshold);
   launch_lines_compact(tr, st->n, at<code_t>(ws, L.code), qhdr(ws), at<StateFast>(ws, L.sfast),
-                       at<double2>(ws, L.srec), at<double>(ws, L.qres), gp, threshold, bp, 1, at<uint64_t>(ws, L.key),
-                       at<uint32_t>(ws, L.sidx1), at<double>(ws, L.Iv), at<uint32_t>(ws, L.bcount), nunit,
-                       at<unsigned long long>(ws, L.maxbits), ws->err, s);
+                       at<double2>(ws, L.srec), at<double>(ws, L.qres), gp, threshold, bp, 1, CAND_BUFFERS(ws, L),
+                       at<uint64_t>(ws, L.key), at<uint32_t>(ws, L.sidx1), at<double>(ws, L.Iv),
+                       at<uint32_t>(ws, L.bcount), nunit, at<unsigned long long>(ws, L.maxbits), ws->err, s);
   tmark(ws, 0, false, s);
   tmark(ws, 1, true, s);
   if (nunit) launch_scan_counts(at<uint32_t>(ws, L.bcount), nunit, cnt + CNT_KEPT, s);
@@ -420,7 +445,7 @@ pxc_status pxc_workspace_create(const pxc_capacity* cap, void* scratch, size_t b
     // defaults: narrow segments balance dense single-condition spectra best; batched
     // tables (most lines zero in most conditions) pay less staging with wide segments
     x->tile[k][0] = 0;
-    x->tile[k][1] = kNumTiles - 1;
+    x->tile[k][1] = kBatchedDefaultTile;
   }
   x->wait_limit = kDefaultWaitLimit;
   cudaStreamCreateWithFlags(&x->cap_stream, cudaStreamNonBlocking);
@@ -586,7 +611,7 @@ pxc_status cross_section_direct(pxc_workspace* ws, const pxc_states* st, const p
   if (!(threshold >= 0.0)) return fail(PXC_ERR_ARG, "threshold must be >= 0");
   for (int i = 0; i < n_c; ++i) {
     if ((r = check_cond(c[i], false, st))) return r;
-    if ((pa->kind & 3) == PXC_LORENTZ && !(c[i].P > 0.0)) return fail(PXC_ERR_ARG, "Lorentzian profile needs P > 0");
+    if (width_kind(pa->kind) == PXC_LORENTZ && !(c[i].P > 0.0)) return fail(PXC_ERR_ARG, "Lorentzian profile needs P > 0");
     if (!(c[i].P >= 0.0)) return fail(PXC_ERR_ARG, "condition: P must be >= 0");
   }
   WsExtra* x = X(ws);
@@ -595,12 +620,15 @@ pxc_status cross_section_direct(pxc_workspace* ws, const pxc_states* st, const p
       n_c > L.max_cond)
     return fail(PXC_ERR_CAPACITY, "cross_section: above workspace capacity");
   if (ws->accumulate && n_c != 1) return fail(PXC_ERR_ARG, "accumulate mode needs n_c == 1");
+  const bool wl = grid->wl_unit > 0.0;
+  if (wl && is_binned(pa->kind)) return fail(PXC_ERR_ARG, "wavelength grids take the sampled profiles only");
   const double wpts = 2.0 * pa->cutoff / grid->dnu + 2.0;
-  const int tile = x->tile[pa->kind][n_c > 1 ? 1 : 0];
+  // wavelength grids: 128-point segments (tile 0), one work item per segment
+  const int tile = wl ? 0 : x->tile[pa->kind][n_c > 1 ? 1 : 0];
   const int seg = tile_seg(tile);
   const int64_t nseg = (grid->n + seg - 1) / seg;
   const int64_t max_partial = L.partial_floats / seg;
-  if (n_c == 1 && wpts > kWinCap) {
+  if (!wl && n_c == 1 && wpts > kWinCap) {
     // the split-item table is sized for windows up to kWinCap points
     const int64_t need = nseg + (int64_t)((double)tr->n * (wpts / seg + 2.0) / kItemLines) + 1;
     if (need > L.max_items || need - nseg > max_partial)
@@ -638,8 +666,9 @@ pxc_status cross_section_direct(pxc_workspace* ws, const pxc_states* st, const p
     const int64_t nunit = (tr->n + kUnitLines - 1) / kUnitLines;
     BoundP bp = make_bound(ws, st, c[0], 0.0);
     launch_lines_compact(tr, st->n, at<code_t>(ws, L.code), qhdr(ws), at<StateFast>(ws, L.sfast),
-                         at<double2>(ws, L.srec), at<double>(ws, L.qres), gp, 0.0, bp, 0, at<uint64_t>(ws, L.key),
-                         idxs[1], nullptr, at<uint32_t>(ws, L.bcount), nunit, nullptr, ws->err, s);
+                         at<double2>(ws, L.srec), at<double>(ws, L.qres), gp, 0.0, bp, 0, CAND_BUFFERS(ws, L),
+                         at<uint64_t>(ws, L.key), idxs[1], nullptr, at<uint32_t>(ws, L.bcount), nunit, nullptr,
+                         ws->err, s);
     if (nunit) launch_scan_counts(at<uint32_t>(ws, L.bcount), nunit, cnt + CNT_KEPT, s);
     launch_compact_staged(at<uint64_t>(ws, L.key), idxs[1], at<uint32_t>(ws, L.bcount), nunit, keys[0], idxs[0], s);
     launch_radix_sort(keys, idxs, cnt + CNT_KEPT, tr->n, at<uint32_t>(ws, L.rcount), s);
@@ -661,9 +690,10 @@ pxc_status cross_section_direct(pxc_workspace* ws, const pxc_states* st, const p
       cudaMemcpyAsync(sigma_exp_out + i, kexp + 2 * slot_of[i], 4, cudaMemcpyDeviceToDevice, s);
   }
   const int ctas = profile_ctas(ws, pa->kind, tile);
+  const bool split = n_c == 1 && !wl;  // only single-condition wavenumber calls split segments
   launch_segments(at<int4>(ws, L.pos), cnt + CNT_KEPT, nseg, seg, at<int32_t>(ws, L.segr), s);
-  launch_items(at<int32_t>(ws, L.segr), nseg, n_c, n_c == 1 ? kItemLines : INT32_MAX / 2, at<int32_t>(ws, L.seg_items),
-               at<Item>(ws, L.items), cnt, L.max_items, n_c == 1 ? 16ll * ctas : 0ll, max_partial, s);
+  launch_items(at<int32_t>(ws, L.segr), nseg, n_c, split ? kItemLines : INT32_MAX / 2, at<int32_t>(ws, L.seg_items),
+               at<Item>(ws, L.items), cnt, L.max_items, split ? 16ll * ctas : 0ll, max_partial, s);
   ProfP p{};
   p.pos = at<int4>(ws, L.pos);
   p.par = at<float2>(ws, L.par);
@@ -683,8 +713,10 @@ pxc_status cross_section_direct(pxc_workspace* ws, const pxc_states* st, const p
   p.err = ws->err;
   p.spin_limit = x->wait_limit;
   p.drain_limit = kDefaultWaitLimit;  // copies in flight always land; this bound is never the one reached
+  p.wl_unit = grid->wl_unit;
   tmark(ws, 2, true, s);
-  launch_profile(p, tile, ctas, s);
+  if (wl) launch_profile_wl(p, (int64_t)n_c * nseg, s);
+  else launch_profile(p, tile, ctas, s);
   tmark(ws, 2, false, s);
   if (n_c == 1)
     launch_reduce_partials(at<Item>(ws, L.items), at<int32_t>(ws, L.seg_items), nseg, seg, 1,
@@ -715,7 +747,7 @@ std::vector<unsigned char> graph_key(pxc_workspace* ws, const pxc_states* st, co
   put(k, tr->upper); put(k, tr->lower); put(k, tr->A); put(k, tr->A_is_f32); put(k, tr->n);
   put(k, n_c);
   for (int i = 0; i < n_c; ++i) { put(k, c[i].T); put(k, c[i].T_vib); put(k, c[i].P); }
-  put(k, grid->nu_min); put(k, grid->dnu); put(k, grid->n);
+  put(k, grid->nu_min); put(k, grid->dnu); put(k, grid->n); put(k, grid->wl_unit);
   put(k, pa->kind); put(k, pa->cutoff); put(k, pa->mass_da); put(k, pa->hwhm); put(k, pa->gamma_ref);
   put(k, pa->n_T); put(k, pa->T_ref);
   put(k, threshold); put(k, sigma_out); put(k, sigma_exp_out);
@@ -840,7 +872,9 @@ pxc_status pxc_cross_section_backward(pxc_workspace* ws, const pxc_states* st, c
   if (ws->accumulate) return fail(PXC_ERR_ARG, "backward: accumulate mode is forward-only");
   if (x->emission || st->n_vib)
     return fail(PXC_ERR_ARG, "backward: absorption with LTE or two-temperature populations only");
-  if (pa->kind & 4) return fail(PXC_ERR_ARG, "backward: sampled profiles only (binned kinds are forward-only)");
+  if (pa->kind > PXC_VOIGT)
+    return fail(PXC_ERR_ARG, "backward: Gaussian, Lorentzian and Voigt only (binned and pseudo-Voigt kinds are forward-only)");
+  if (grid->wl_unit != 0.0) return fail(PXC_ERR_ARG, "backward: wavenumber grids only");
   GridP gp = make_gridp(*grid, pa->cutoff);
   unsigned long long* cnt = at<unsigned long long>(ws, L.counters);
   cudaMemsetAsync(cnt, 0, CNT_N * 8, s);
@@ -1041,7 +1075,8 @@ pxc_status pxc_cross_section_streamed(pxc_workspace* ws, const pxc_states* st, c
   if (!ws || !h_up || !h_lo || !h_A || n_lines < 0 || !c || !grid || !pa || !buf0 || !buf1 || !sigma_out ||
       !sigma_exp_out)
     return fail(PXC_ERR_ARG, "streamed: bad arguments");
-  const bool broad = pa->kind == PXC_LORENTZ || pa->kind == PXC_VOIGT;
+  const int wk = width_kind(pa->kind);
+  const bool broad = wk == PXC_LORENTZ || wk == PXC_VOIGT;
   if (broad && (!h_gref || !h_nT)) return fail(PXC_ERR_ARG, "streamed: gamma_ref and n_T required");
   const int64_t chunk = ws->cap.max_lines;
   if (chunk < 1) return fail(PXC_ERR_CAPACITY, "streamed: workspace has no line capacity");

@@ -43,7 +43,11 @@ constexpr int kThreadsQ = 256;
 // Profile kernel tiles: segment widths are a runtime choice among the compiled configurations
 // (see kernels_profile.cu); the workspace is sized for the narrowest and the widest.
 constexpr int kNumTiles = 4;
-constexpr int kNumKinds = 8;
+constexpr int kBatchedDefaultTile = 3;  // 2048-point segments
+constexpr int kNumKinds = 11;
+// Profile kinds (pxc_profile): sampled 0..3, binned 4..7, pseudo-Voigt 8..10.
+__host__ __device__ constexpr bool is_binned(int kind) { return kind >= 4 && kind <= 7; }
+__host__ __device__ constexpr bool is_pseudo_voigt(int kind) { return kind >= 8 && kind <= 10; }
 constexpr long long kDefaultWaitLimit = 4000000000ll;  // ~2 s of clock cycles             // sampled and binned profile kinds (pxc_profile)
 constexpr int kSegMin = 128;
 constexpr int kSegMax = 2048;

@@ -414,3 +414,31 @@ def test_prefilter_keeps_exact_set_at_window_and_threshold_edges(pxc, seed, q, o
     perm, _, _ = ws.binning(s["n_kept"], s["n_segments"])
     assert np.array_equal(perm.cpu().numpy(), r["perm"])
     H.check_sigma(H.sigma_phys(sig[0], e[0].item()), r["sigma"], f"prefilter edges {seed}")
+
+
+def test_lines_near_zero_wavenumber(pxc):
+    """Lines with nu from 5e-4 to 30 cm^-1 on a grid starting at 0: the Doppler width is at its
+    floor and one grid step spans up to ~1e5 Doppler widths, so every profile path meets |x| up to
+    ~1e8 (and |x| + y < 15 near the centre at low pressure).  sigma stays finite and matches."""
+    E = np.array([0.0, 0.0005, 0.0013, 0.02, 0.2, 3.0, 30.0])
+    g = np.array([1, 3, 5, 3, 5, 7, 9], np.int32)
+    up = np.arange(1, E.size, dtype=np.int32)
+    lo = np.zeros(up.size, np.int32)
+    A = np.full(up.size, 1e-3)
+    w = H.synth.workload("voigt_1e9").scaled(n_states=E.size, n_trans=up.size, nu_min=0.0, dnu=0.01, n_grid=100_001,
+                                              T=2000.0, threshold=0.0)
+    c = {"w": w, "E": E, "g": g, "Ev": np.zeros(E.size), "up": up, "lo": lo, "A": A,
+         "gr": np.full(up.size, 0.05, np.float32), "ne": np.full(up.size, 0.5, np.float32)}
+    st, tr, _, grid = H.device(c)
+    for kind in ("voigt", "lorentz", "gauss_doppler"):
+        _, _, prof, _ = H.device(c, kind)
+        for P in (1e-5, 1e-2, 1.0):
+            for tile in range(pxc.NUM_TILES):
+                ws = _ws(pxc, c)
+                ws.set_tile(pxc.PROFILES[kind], False, tile)
+                sig, e = pxc.pxc_cross_section(ws, st, tr, (w.T, 0.0, P), grid, prof)
+                ws.sync()
+                got = H.sigma_phys(sig[0], e[0].item())
+                assert np.isfinite(got).all(), (kind, P, tile)
+                r = H.oracle_run(c, kind=kind, P=P, threshold=0.0)
+                H.check_sigma(got, r["sigma"], f"{kind} P={P} tile {tile}")

@@ -95,7 +95,7 @@ def test_autotune_picks_a_tile_and_keeps_result(pxc, poly, poly_ref):
     assert 0 <= tile < pxc.NUM_TILES
     assert all(m > 0 for m in ms) and ms[tile] == min(ms)
     assert ws.get_tile(3, False) == tile
-    assert ws.get_tile(3, True) == pxc.NUM_TILES - 1  # the batched choice is untouched
+    assert ws.get_tile(3, True) == pxc.BATCHED_DEFAULT_TILE  # the batched choice is untouched
     H.check_sigma(H.sigma_phys(sig[0], e[0].item()), poly_ref["voigt"], "autotuned")
     # the next plain call uses the chosen tile
     pxc.pxc_cross_section(ws, st, tr, (w.T, 0.0, w.P), grid, prof, 0.0)
@@ -104,7 +104,7 @@ def test_autotune_picks_a_tile_and_keeps_result(pxc, poly, poly_ref):
 
 def test_tile_arguments_checked(pxc, poly):
     ws = _ws(pxc, poly)
-    for args in [(8, False, 0), (-1, False, 0), (0, False, pxc.NUM_TILES), (0, False, -1)]:
+    for args in [(11, False, 0), (-1, False, 0), (0, False, pxc.NUM_TILES), (0, False, -1)]:
         with pytest.raises(pxc.PxcError) as ei:
             ws.set_tile(*args)
         assert ei.value.code == 1
