@@ -558,6 +558,11 @@ def run_extras(args, pxc, torch, dev, synth):
     tile_b, tune_b, _, _ = pxc.pxc_autotune(wsb, st, tr, conds, grid, prof, 0.0, repeats=1, sigma=sig, sigma_exp=se)
     ms_b = timed(lambda: pxc.pxc_cross_section(wsb, st, tr, conds, grid, prof, 0.0, sigma=sig, sigma_exp=se))
     sb = wsb.stats()
+    # the same table replayed from a captured CUDA graph (the first call captures)
+    wsb.set_graphs(True)
+    ms_g = timed(lambda: pxc.pxc_cross_section(wsb, st, tr, conds, grid, prof, 0.0, sigma=sig, sigma_exp=se), reps=3)
+    gstats = wsb.graph_stats()
+    wsb.set_graphs(False)
     del wsb
     wsp = pxc.Workspace(max_states=w.n_states, max_lines=w.n_trans, max_grid=w.n_grid, device=dev)
     s1 = torch.empty(1, w.n_grid, dtype=torch.float32, device=dev)
@@ -577,7 +582,8 @@ def run_extras(args, pxc, torch, dev, synth):
         b = torch.ldexp(s1[0].double(), e1[0].double())
         worst = max(worst, float((a - b).abs().max() / b.abs().max().clamp_min(1e-300)))
     res["batched_table"] = {"workload": w.name, "conditions": len(conds), "lines": w.n_trans,
-                            "batched_ms": ms_b, "sequential_ms": ms_s, "speedup": ms_s / ms_b,
+                            "batched_ms": ms_b, "graph_replay_ms": ms_g, "graph": gstats,
+                            "sequential_ms": ms_s, "speedup": ms_s / ms_b,
                             "max_abs_diff_rel_peak": worst, "kept_lines": sb["n_kept"],
                             "tile_batched": tile_b, "autotune_batched_ms": tune_b, "tile_sequential": tile_s}
     del wsp, st, tr, prof, sig
@@ -602,8 +608,13 @@ def run_extras(args, pxc, torch, dev, synth):
         pxc.pxc_cross_section_backward(wsf, st, tr, cond, grid, prof, wt)
 
     ms_fb = timed(fb, reps=3)
+    ev_f = wsf.stats()["evals_nonzero"]
+    ms_bwd = max(ms_fb - ms_f, 1e-6)
     res["fwd_bwd"] = {"workload": w.name, "lines": w.n_trans, "fwd_ms": ms_f, "fwd_bwd_ms": ms_fb,
-                      "ratio": ms_fb / ms_f}
+                      "ratio": ms_fb / ms_f, "evals": ev_f, "fwd_evals_per_s": ev_f / (ms_f / 1e3),
+                      "bwd_evals_per_s": ev_f / (ms_bwd / 1e3),
+                      "note": "backward = adjoint pass (intensity, sort and one k_adjoint launch); its evaluations "
+                              "are the forward's, each with the W4 value and its z-derivative"}
 
     # vibronic-density populations on the same list (T_rot = 1200 K), absorption and emission
     nv = torch.from_numpy(w.vib_densities()).to(dev)
