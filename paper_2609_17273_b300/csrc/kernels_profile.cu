@@ -229,6 +229,10 @@ __device__ __forceinline__ float region_one(float u, float K, float e) {
 // LineC::masks bit set when a line's region-I terms in a warp need region_one (|x| or y >= 1e9);
 // otherwise the direct K (u + 1) / (u^2 + e), one reciprocal, is used.
 constexpr int kWideRange = 8;
+// LineC::masks bit set when every |x| of a line in a warp is below 1e4: region II's quartic in
+// x^2 then stays far inside the FP32 range, and the core and mid paths use it for every point
+// with |x| + y >= 5.5 (it is at least as accurate as region I there), one path fewer.
+constexpr int kRegion2Everywhere = 16;
 __device__ __forceinline__ float region_one_or_direct(float u, float K, float e, int masks) {
   return (masks & kWideRange) ? region_one(u, K, e) : fmaf(u, K, K) * frcp(fmaf(u, u, e));
 }
@@ -664,7 +668,8 @@ __device__ __forceinline__ void eval_mid(const LineC& c, int wbase, int lane, fl
     const float x = fmaf((float)k, s32, x0);
     const float X = x * x;
     float v;
-    if (fabsf(x) + c.y >= 15.f) {  // region I: the quartic below would overflow FP32 for very large x
+    if (!(c.masks & kRegion2Everywhere) && fabsf(x) + c.y >= 15.f) {  // region I: the quartic below
+                                                                      // would overflow FP32 for very large x
       v = region_one_or_direct(X + c.B1, c.K, c.d, c.masks);
     } else {
       const float N = fmaf(fmaf(fmaf(r.n3, X, r.n2), X, r.n1), X, r.n0);
@@ -675,8 +680,9 @@ __device__ __forceinline__ void eval_mid(const LineC& c, int wbase, int lane, fl
   }
 }
 
-// Warps near the line core (Voigt), some point with |x| + y < 5.5.  Points with |x| + y >= 15 take
-// region I, points with 5.5 <= |x| + y < 15 W4's region-II formula, the real rational
+// Warps near the line core (Voigt), some point with |x| + y < 5.5.  Points with |x| + y >= 5.5 take
+// W4's region-II formula (region I instead beyond 15 when the warp's |x| reaches 1e4, where the
+// region-II quartic would leave the FP32 range), the real rational
 // Re w = y N(X) / D(X) in X = x^2 (N cubic, D monic quartic, coefficients from Y = y^2 once per line
 // and warp; Humlicek's constants satisfy a = 2.5 b, which gives the factored forms of region2).
 // Points with |x| + y < 5.5 take one formula per line where one
@@ -684,8 +690,8 @@ __device__ __forceinline__ void eval_mid(const LineC& c, int wbase, int lane, fl
 // FP32 against scipy's wofz: <= 4.8e-5 relative wherever Re w > 1e-6 of its peak, below W4's own
 // region III/IV split, 9.1e-5), for y >= 0.9 the region-III rational (<= 3.8e-5; that whole disc
 // is region III), and W4's region III/IV test per point in between.  A block then follows at most
-// three paths instead of four.  Blocks of 32 points whose nearest point is beyond the
-// region-I reach keep the region-I formula (a uniform branch).
+// two paths instead of four.  With 8 or more points per lane, blocks of 32 points whose nearest
+// point is beyond the region-I reach keep the region-I formula (a uniform branch).
 template <int KIND, int PTS>
 __device__ __forceinline__ void eval_slow(const LineC& c, int wbase, int lane, const float* lk, float* acc) {
   if (is_binned(KIND)) return;  // binned lines are never in the core class
@@ -700,8 +706,9 @@ __device__ __forceinline__ void eval_slow(const LineC& c, int wbase, int lane, c
     const int li = b0 + lane;
     const bool in = (unsigned)(li - c.lo) <= span;
     const float dmin = fmaxf(0.f, fmaxf(c.cen - (float)(b0 + 31), (float)b0 - c.cen));
-    if (dmin > c.reach) {
-      // the whole block is in region I (uniform branch): the fast-path formula
+    if (PTS >= 8 && dmin > c.reach) {
+      // the whole block is in region I (uniform branch): the fast-path formula (measured to pay
+      // off for wide warps only; narrow ones rarely have such blocks among their core lines)
       const float x = fmaf(lk[k], c.b, c.a);
       acc[k] += in ? region_one_or_direct(fmaf(x, x, c.B1), c.K, c.d, c.masks) : 0.f;
       continue;
@@ -709,7 +716,7 @@ __device__ __forceinline__ void eval_slow(const LineC& c, int wbase, int lane, c
     const float x = fmaf((float)li - c.pf, c.step, c.nfs);
     const float sx = fabsf(x) + c.y;
     float v;
-    if (sx >= 15.f) {
+    if (sx >= 15.f && !(c.masks & kRegion2Everywhere)) {
       // region I (the region-II quartic in x^2 would leave the FP32 range for very large x)
       v = region_one_or_direct(fmaf(x, x, c.B1), c.K, c.d, c.masks);
     } else if (sx >= 5.5f) {
@@ -831,6 +838,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_profile(const ProfP p) {
         if (KIND == PXC_VOIGT && cls >= 2) {
           const float dmax = fmaxf(fabsf(c.cen - (float)wbase), fabsf(c.cen - (float)(wbase + WPTS - 1)));
           if (dmax * c.step > 1e9f || c.y > 1e9f) c.masks |= kWideRange;
+          if (dmax * c.step < 1e4f && c.y < 15.f) c.masks |= kRegion2Everywhere;
         }
         const unsigned bf = __ballot_sync(0xffffffffu, cls == 1);
         const unsigned bo = __ballot_sync(0xffffffffu, cls >= 2);  // cls: the class before the range flag
