@@ -245,6 +245,8 @@ def main_pxc(args):
     conds = _conditions(w)
     n_c = len(conds)
     batched = n_c > 1
+    if args.backward and (batched or (w.chunk and w.chunk < w.n_trans)):
+        raise SystemExit("--backward needs a single-condition workload held in one chunk")
     chunk = w.chunk or w.n_trans
     nchunks = (w.n_trans + chunk - 1) // chunk
     states_h = w.states()
@@ -296,7 +298,19 @@ def main_pxc(args):
                            d_ne[sl] if broad else None)
         return tr, prof
 
+    wgt = torch.from_numpy(w.weights()).to(dev) if args.backward else None
+
     def step(count=None):
+        if args.backward:
+            # forward and the adjoint of L = sum_i w_i sigma_i (one condition, no chunks)
+            tr, prof = chunk_args(0)
+            pxc.pxc_cross_section(ws, states, tr, cond_arg, grid, prof, w.threshold, sigma=sigma, sigma_exp=sexp)
+            pxc.pxc_cross_section_backward(ws, states, tr, cond_arg, grid, prof, wgt, w.threshold)
+            if count is not None:
+                s = ws.stats()
+                count["evals"] += s["evals_nonzero"]; count["evals_window"] += s["evals_window"]
+                count["kept"] += s["n_kept"]
+            return
         ws.set_accumulate(nchunks > 1)
         if nchunks > 1:
             sigma.zero_()
@@ -374,7 +388,7 @@ def main_pxc(args):
 
     # ---------------------------------------------------------------- e2e through the public API, host buffers
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not args.backward:
         h_sig = torch.empty(n_c, w.n_grid, dtype=torch.float32, pin_memory=True)
         h_exp = torch.empty(n_c, dtype=torch.int32, pin_memory=True)
         asz = 4 if w.A_f32 else 8
@@ -472,6 +486,7 @@ def main_pxc(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": w.name, "lines": w.n_trans, "states": w.n_states, "grid": w.n_grid,
                       "chunk": chunk, "conditions": n_c, "profile": w.profile, "T": w.T, "T_vib": w.T_vib,
+                      "step": "forward + adjoint" if args.backward else "forward",
                       "P": w.P, "cutoff": w.cutoff, "threshold": w.threshold,
                       "parallelism": f"replicas x{world}",
                       "l2": f"inputs ({w.n_trans * (16 if w.A_f32 else 20) / 1e9:.1f} GB) larger than L2"
@@ -677,6 +692,8 @@ def main():
     ap.add_argument("--lines", type=int, default=0, help="override the transition count (smaller runs)")
     ap.add_argument("--extras-lines", type=int, default=0, help="override the batched-table transition count")
     ap.add_argument("--tile", type=int, default=-1, help="profile tile configuration (-1: autotune on chunk 0)")
+    ap.add_argument("--backward", action="store_true",
+                    help="each step is the forward call and its adjoint (single-condition workloads in one chunk)")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

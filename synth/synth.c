@@ -10,7 +10,7 @@
  * to (seed, stream, counter), so any slice of a list can be regenerated
  * independently and the result does not depend on the thread count.
  *
- * Level schemes (readings of the workload descriptions, stated in the design doc):
+ * Level schemes (readings of the workload descriptions, which leave these open):
  *  - diatomic: E(v,J) = 2000 v + 10 x - 1e-3 min(x, 5000)^2 with x = J(J+1)
  *    (clamped so the rotational energy keeps increasing past J ~ 70), or the
  *    literal quartic when `literal` is set; g = 3(2J+1); E_vib(v) = E(v, 0).
