@@ -44,8 +44,12 @@ EVAL_MUFU = 1
 L2_BYTES = 126 * 2 ** 20
 
 # DRAM traffic per launch from a committed ncu capture, valid only for the kernel source it was
-# taken on (sha256 prefix of the .cu file); scaled to one 1e8-line launch (see profiles/).
-NCU_TRAFFIC = {}
+# taken on (sha256 prefix of the .cu file); scaled to one 1e8-line launch of voigt_1e9 from the
+# 2e7-line capture (profiles/k_profile_voigt_2e7_lines.md, profiles/k_lines_voigt_2e7_lines.md).
+NCU_TRAFFIC = {
+    ("profile", "a4ed75d62ec9c499"): 13.80e6 * 5,               # k_profile<voigt>, tile 0
+    ("intensity", "71d21a09c89640eb"): (793.9e6 + 383.2e6) * 5,  # k_lines_pre + k_lines_exact
+}
 
 
 def _src_hash(rel):
@@ -467,16 +471,17 @@ def main_pxc(args):
                               "note": "warp-instruction issue slots of the algorithmic work (one per SMSP per clock)"},
                     "launch_ms": prof_launch_ms, "launches_per_step": prof_n / max(args.steps, 1)}
     # algorithmic bytes of one intensity launch: the line arrays read once (upper, lower, A),
-    # (key, index, FP64 I) written per kept line, and the 2-byte state-code table read once
+    # (key, index, FP64 I) written per kept line, and the state-code table (12-bit codes, 3 bytes
+    # per 2 states) read once
     kept_per_launch = kept / nchunks
     a_bytes = 4 if w.A_f32 else 8
-    per_launch_bytes = chunk * (4 + 4 + a_bytes) + kept_per_launch * (8 + 4 + 8) + w.n_states * 2
+    per_launch_bytes = chunk * (4 + 4 + a_bytes) + kept_per_launch * (8 + 4 + 8) + (w.n_states + 1) // 2 * 3
     int_launch_ms = int_ms / max(int_n, 1)
     ach_hbm = per_launch_bytes / (int_launch_ms / 1e3) / 1e9 if int_n else 0.0
     roof_int = {"bound": "hbm", "achieved": ach_hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach_hbm / peaks["hbm_gbs"], "traffic": NCU_TRAFFIC.get(
                     ("intensity", _src_hash("paper_2609_17273_b300/csrc/kernels_lines.cu"))),
-                "kernel": "k_lines_c", "peak_source": f"hbm_gbs of {peak_src} MEASURED_PEAKS.json",
+                "kernel": "k_lines_pre + k_lines_exact", "peak_source": f"hbm_gbs of {peak_src} MEASURED_PEAKS.json",
                 "bytes_per_line": per_launch_bytes / chunk,
                 "sector_bytes_per_line": 4 + 4 + a_bytes + 2 * 32, "launch_ms": int_launch_ms}
     dominant = roof_profile if prof_ms >= int_ms else roof_int
