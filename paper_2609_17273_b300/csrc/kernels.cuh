@@ -8,7 +8,7 @@ namespace pxc {
 // non-zero scaled intensity, window evaluations (all / non-zero lines), line-segment pairs, raw
 // item total; CNT_N slots in all.
 enum { CNT_QUEUE = 0, CNT_ITEMS = 1, CNT_KEPT = 2, CNT_NONZERO = 3, CNT_EVALS = 4, CNT_EVALS_NZ = 5, CNT_ALL = 6,
-       CNT_ITEMS_RAW = 7, CNT_N = 16 };
+       CNT_ITEMS_RAW = 7, CNT_SLOT_NZ = 8, CNT_N = 16 };
 
 
 // Host-side argument checks and per-condition constants shared by every entry point
@@ -106,7 +106,7 @@ struct BoundP {
 // which need max_lines entries and one count per unit) and exact selection (kept lines staged per
 // unit into kstage / istage, counts into ucount, FP64 intensities by transition index into Iv).
 void launch_lines_compact(const pxc_transitions* tr, int64_t ns, const code_t* code, const QuantHdr* qh,
-                          const StateFast* sfast, const double2* srec,
+                          const StateFast* sfast,
                           const double* qres, const GridP& gp, double threshold, const BoundP& bp, int with_I,
                           uint32_t* cand_t, uint64_t* cand_ul, uint64_t* cand_a, uint32_t* ccount,
                           uint64_t* kstage, uint32_t* istage, double* Iv, uint32_t* ucount, int64_t nunit,
@@ -148,9 +148,15 @@ void launch_scale(const double* sI, const unsigned long long* n_dev, int64_t n_m
 void launch_segments(const int4* pos, const unsigned long long* n_dev, int64_t nseg, int seg, int32_t* segr,
                      cudaStream_t s);
 
+// cond_list: the condition of each group of nseg items (n_c entries), or null for 0 .. n_c-1.
 void launch_items(const int32_t* segr, int64_t nseg, int n_c, int item_lines, int32_t* seg_items,
                   Item* items, unsigned long long* counters, int64_t max_items, int64_t target_items,
-                  int64_t max_partial, cudaStream_t s);
+                  int64_t max_partial, const int32_t* cond_list, cudaStream_t s);
+// Stable compaction of the first *n_dev sorted lines with non-zero scaled intensity Is into
+// pos_c / par_c / Is_c (count to *nnz_dev); bcount needs n_max / kUnitLines + 2 entries.
+void launch_compact_nonzero(const int4* pos, const float2* par, const float* Is, const unsigned long long* n_dev,
+                            int64_t n_max, uint32_t* bcount, unsigned long long* nnz_dev, int4* pos_c, float2* par_c,
+                            float* Is_c, cudaStream_t s);
 
 void launch_reduce_partials(const Item* items, const int32_t* seg_items, int64_t nseg, int seg, int n_c,
                             const float* partial, float* sigma, int64_t n_grid, cudaStream_t s);
@@ -212,8 +218,10 @@ struct AdjP {
   double* lineP;
 };
 void launch_adjoint(const AdjP& p, cudaStream_t s);
+// Fixed-order FP64 sums of the per-line shares; `scratch` holds adjoint_reduce_scratch_bytes().
+size_t adjoint_reduce_scratch_bytes();
 void launch_adjoint_reduce(const double* lineT, const double* lineTv, const double* lineP,
-                           const unsigned long long* n_dev, int64_t n_max, double* outT, double* outTv,
+                           const unsigned long long* n_dev, double* scratch, double* outT, double* outTv,
                            double* outP, cudaStream_t s);
 
 }  // namespace pxc

@@ -64,6 +64,42 @@ __device__ __forceinline__ T warp_sum(T v) {
 }
 
 // ------------------------------------------------------------------ K-Q: Boltzmann table and Q
+// e^x for the Boltzmann factors by Tang's table-driven method (ACM TOMS 15 (1989) 144-157):
+// x = (64 m + j) ln2/64 + r with |r| <= ln2/128, e^x = 2^m 2^(j/64) e^r, e^r - 1 from its degree-5
+// Taylor polynomial (the first omitted term is below 2^-54 of e^r), 2^(j/64) from a table of the
+// correctly rounded values (evaluated in 60-digit decimal arithmetic).  About half the FP64
+// operations of exp(); within ~1 ulp.  |x| >= 700 (the under- and overflow ranges, NaN) uses exp().
+__device__ const double kExp2J64[64] = {
+    0x1.0000000000000p+0, 0x1.02c9a3e778061p+0, 0x1.059b0d3158574p+0, 0x1.0874518759bc8p+0,
+    0x1.0b5586cf9890fp+0, 0x1.0e3ec32d3d1a2p+0, 0x1.11301d0125b51p+0, 0x1.1429aaea92de0p+0,
+    0x1.172b83c7d517bp+0, 0x1.1a35beb6fcb75p+0, 0x1.1d4873168b9aap+0, 0x1.2063b88628cd6p+0,
+    0x1.2387a6e756238p+0, 0x1.26b4565e27cddp+0, 0x1.29e9df51fdee1p+0, 0x1.2d285a6e4030bp+0,
+    0x1.306fe0a31b715p+0, 0x1.33c08b26416ffp+0, 0x1.371a7373aa9cbp+0, 0x1.3a7db34e59ff7p+0,
+    0x1.3dea64c123422p+0, 0x1.4160a21f72e2ap+0, 0x1.44e086061892dp+0, 0x1.486a2b5c13cd0p+0,
+    0x1.4bfdad5362a27p+0, 0x1.4f9b2769d2ca7p+0, 0x1.5342b569d4f82p+0, 0x1.56f4736b527dap+0,
+    0x1.5ab07dd485429p+0, 0x1.5e76f15ad2148p+0, 0x1.6247eb03a5585p+0, 0x1.6623882552225p+0,
+    0x1.6a09e667f3bcdp+0, 0x1.6dfb23c651a2fp+0, 0x1.71f75e8ec5f74p+0, 0x1.75feb564267c9p+0,
+    0x1.7a11473eb0187p+0, 0x1.7e2f336cf4e62p+0, 0x1.82589994cce13p+0, 0x1.868d99b4492edp+0,
+    0x1.8ace5422aa0dbp+0, 0x1.8f1ae99157736p+0, 0x1.93737b0cdc5e5p+0, 0x1.97d829fde4e50p+0,
+    0x1.9c49182a3f090p+0, 0x1.a0c667b5de565p+0, 0x1.a5503b23e255dp+0, 0x1.a9e6b5579fdbfp+0,
+    0x1.ae89f995ad3adp+0, 0x1.b33a2b84f15fbp+0, 0x1.b7f76f2fb5e47p+0, 0x1.bcc1e904bc1d2p+0,
+    0x1.c199bdd85529cp+0, 0x1.c67f12e57d14bp+0, 0x1.cb720dcef9069p+0, 0x1.d072d4a07897cp+0,
+    0x1.d5818dcfba487p+0, 0x1.da9e603db3285p+0, 0x1.dfc97337b9b5fp+0, 0x1.e502ee78b3ff6p+0,
+    0x1.ea4afa2a490dap+0, 0x1.efa1bee615a27p+0, 0x1.f50765b6e4540p+0, 0x1.fa7c1819e90d8p+0,
+};
+
+__device__ __forceinline__ double exp_tang(double x, const double* __restrict__ tab) {
+  const long long xb = __double_as_longlong(x);
+  if ((xb & 0x7fffffffffffffffll) >= 0x4085e00000000000ll) return exp(x);  // |x| >= 700 or NaN
+  const double n = rint(x * 92.332482616893657);                           // 64 / ln2
+  const int ni = (int)n;
+  const double r = fma(-n, 0x1.abc9e3b39803fp-62, fma(-n, 0x1.62e42fefa39efp-7, x));  // ln2/64, two parts
+  const double q = r * fma(fma(fma(fma(r, 1.0 / 120.0, 1.0 / 24.0), r, 1.0 / 6.0), r, 0.5), r, 1.0);
+  const double t = tab[ni & 63];
+  const double v = fma(t, q, t);  // in [0.99, 1.99]
+  return __longlong_as_double(__double_as_longlong(v) + ((long long)(ni >> 6) << 52));
+}
+
 // b_s = exp(-c2 E_s / T) (LTE, Eq. pf), exp(-c2 E_vib/T_vib - c2 E_rot/T_rot) (Eq. Q nlte 2T) or
 // n_vib exp(-c2 E_rot / T_rot) (vibronic densities, Eq. Q nlte Nvib); per-block partial sums of
 // g b, g b E_rot, g b E_vib and (cooling function) g b S in a fixed order.
@@ -76,6 +112,9 @@ __global__ void __launch_bounds__(kThreadsQ) k_boltzmann(const double* __restric
                                                          const double* __restrict__ Ssum,
                                                          double* __restrict__ qpart, unsigned* err) {
   __shared__ double red[kThreadsQ / 32][kQMoments];
+  __shared__ double tab[64];
+  if (threadIdx.x < 64) tab[threadIdx.x] = kExp2J64[threadIdx.x];
+  __syncthreads();
   for (int sl = 0; sl < nslot; ++sl) {
     const SlotP sp = slots[sl];
     const bool two_t = sp.c2_Tv > 0.0;
@@ -112,7 +151,7 @@ __global__ void __launch_bounds__(kThreadsQ) k_boltzmann(const double* __restric
         if (x > kExpMax) {
           bad |= ERRB_OVERFLOW;
         } else {
-          b = w * exp(x);
+          b = w * exp_tang(x, tab);
           lb = x * 1.4426950408889634;
           if (dens) lb += log2(w);
           double term = (double)g[s] * b;
@@ -126,8 +165,10 @@ __global__ void __launch_bounds__(kThreadsQ) k_boltzmann(const double* __restric
       if (sfast) {
         StateFast r;
         r.E = e;
+        r.b = b;
         r.g = g[s];
         r.lb = (float)lb;
+        r.pad = 0;
         sfast[s] = r;
       }
     }
@@ -427,17 +468,20 @@ __device__ __forceinline__ uint32_t block_rank(bool flag, uint32_t* wsum, uint32
   return before + __popc(m & ((1u << lane) - 1u));
 }
 
-// 12-bit code of state s (two byte loads of one sector, kept in L2 with the evict-last policy: the
-// state codes are re-read at random).
+// 12-bit code of state s (kept in L2 with the evict-last policy: the state codes are re-read at
+// random).  A pair of states shares 3 bytes: state 2k is byte 3k plus the low nibble of byte 3k+1,
+// state 2k+1 the high nibble of byte 3k+1 plus byte 3k+2; either way two consecutive bytes starting
+// at 3k + (s & 1), loaded without a branch so that every code load of a round is in flight at once.
 __device__ __forceinline__ int ld_byte(const code_t* p, uint64_t pol) {
   unsigned short v;
-  asm volatile("ld.global.nc.L2::cache_hint.u8 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(pol));
+  asm("ld.global.nc.L2::cache_hint.u8 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(pol));
   return (int)v;
 }
 __device__ __forceinline__ int ld_code(const code_t* tab, int32_t s, uint64_t pol) {
-  const code_t* p = tab + 3 * (int64_t)(s >> 1);
-  if (s & 1) return (ld_byte(p + 1, pol) >> 4) | (ld_byte(p + 2, pol) << 4);
-  return ld_byte(p, pol) | ((ld_byte(p + 1, pol) & 0xf) << 8);
+  const int odd = s & 1;
+  const code_t* p = tab + 3 * (int64_t)(s >> 1) + odd;
+  const int b0 = ld_byte(p, pol), b1 = ld_byte(p + 1, pol);
+  return odd ? (b0 >> 4) | (b1 << 4) : b0 | ((b1 & 0xf) << 8);
 }
 
 // Per-block constants of the compacting intensity pass (computed once per CTA by one thread).
@@ -480,31 +524,30 @@ __device__ LinesConst lines_const(const code_t* code, const QuantHdr* qhp, const
   return c;
 }
 
-// Loads line t (streaming: upper, lower, A) and decides whether it is a candidate: valid ids and,
-// when the codes are on, a code-bound nu inside the kept window and (LTE with a threshold) a code
-// bound on |I| at or above the threshold.  Bad ids and non-finite A are reported in `bad`.
-__device__ __forceinline__ bool line_candidate(int64_t t, const int32_t* __restrict__ up,
-                                               const int32_t* __restrict__ lo, const void* __restrict__ Av, int A32,
-                                               int64_t ns, const code_t* __restrict__ code, const LinesConst& c,
-                                               const BoundP& bp, uint64_t pol, int32_t* u_out, int32_t* l_out,
-                                               unsigned long long* ab_out, unsigned* bad) {
-  const int32_t u = __ldcs(up + t), l = __ldcs(lo + t);
-  float Af;
-  bool finite;
+// One line's inputs as streamed: upper and lower ids and the bit pattern of A (FP32 or FP64).
+struct LineIn {
+  int32_t u, l;
   unsigned long long ab;
-  if (A32) {
-    Af = __ldcs((const float*)Av + t);
-    ab = __float_as_uint(Af);
-    finite = (ab & 0x7f800000u) != 0x7f800000u;
-  } else {
-    const double A = __ldcs((const double*)Av + t);
-    ab = (unsigned long long)__double_as_longlong(A);
-    finite = (ab & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
-    Af = (float)A;
-  }
-  *u_out = u;
-  *l_out = l;
-  *ab_out = ab;
+};
+
+__device__ __forceinline__ LineIn line_load(int64_t t, const int32_t* __restrict__ up, const int32_t* __restrict__ lo,
+                                            const void* __restrict__ Av, int A32) {
+  LineIn x;
+  x.u = __ldcs(up + t);
+  x.l = __ldcs(lo + t);
+  x.ab = A32 ? (unsigned long long)__float_as_uint(__ldcs((const float*)Av + t))
+             : (unsigned long long)__double_as_longlong(__ldcs((const double*)Av + t));
+  return x;
+}
+
+// Whether a loaded line is a candidate: valid ids and, when the codes are on, a code-bound nu inside
+// the kept window and (LTE with a threshold) a code bound on |I| at or above the threshold.  Bad ids
+// and non-finite A are reported in `bad`.
+__device__ __forceinline__ bool line_test(const LineIn& x, int A32, int64_t ns, const code_t* __restrict__ code,
+                                          const LinesConst& c, const BoundP& bp, uint64_t pol, unsigned* bad) {
+  const int32_t u = x.u, l = x.l;
+  const bool finite = A32 ? (x.ab & 0x7f800000ull) != 0x7f800000ull
+                          : (x.ab & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
   if (u < 0 || u >= ns || l < 0 || l >= ns) {
     *bad |= ERRB_ID;
     return false;
@@ -516,6 +559,7 @@ __device__ __forceinline__ bool line_candidate(int64_t t, const int32_t* __restr
   const int d = qu - ql;
   if (d < c.dlo || d > c.dhi) return false;
   if (c.pre_thr && d > 3) {
+    const float Af = A32 ? __uint_as_float((unsigned)x.ab) : (float)__longlong_as_double((long long)x.ab);
     const float kl2e = 1.4426950408889634f;
     const float nul = (float)(d - 3) * c.lo_scale, nuh = (float)(d + 3) * c.hi_scale;
     const float m = fminf(1.f, bp.c2_T * nuh);
@@ -559,18 +603,21 @@ __global__ void __launch_bounds__(kThreadsI, 8) k_lines_pre(const int32_t* __res
   const int64_t ubase = unit * kUnitLines;
   unsigned bad = 0;
   uint32_t nb = 0;
+  // the next round's line arrays are requested before this round's code gathers, so the two
+  // memory latencies of a round overlap
+  LineIn nx{0, 0, 0ull};
+  if (ubase + lane < n) nx = line_load(ubase + lane, up, lo, Av, A32);
   for (int r = 0; r < kUnitLines / 32; ++r) {
     const int64_t t = ubase + r * 32 + lane;
-    bool cand = false;
-    int32_t u = 0, l = 0;
-    unsigned long long ab = 0;
-    if (t < n) cand = line_candidate(t, up, lo, Av, A32, ns, code, c, bp, pol, &u, &l, &ab, &bad);
+    const LineIn x = nx;
+    if (r + 1 < kUnitLines / 32 && t + 32 < n) nx = line_load(t + 32, up, lo, Av, A32);
+    const bool cand = t < n && line_test(x, A32, ns, code, c, bp, pol, &bad);
     const unsigned cm = __ballot_sync(0xffffffffu, cand);
     if (cand) {
       const int64_t o = ubase + nb + __popc(cm & lt);
       cand_t[o] = (uint32_t)t;
-      cand_ul[o] = ((uint64_t)(uint32_t)u << 32) | (uint32_t)l;
-      cand_a[o] = ab;
+      cand_ul[o] = ((uint64_t)(uint32_t)x.u << 32) | (uint32_t)x.l;
+      cand_a[o] = x.ab;
     }
     nb += __popc(cm);
   }
@@ -583,8 +630,7 @@ __global__ void __launch_bounds__(kThreadsI) k_lines_exact(const int32_t* __rest
                                                            const void* __restrict__ Av, int A32, int64_t n,
                                                            const code_t* __restrict__ code,
                                                            const QuantHdr* __restrict__ qhp,
-                                                           const StateFast* __restrict__ sfast,
-                                                           const double2* __restrict__ srec, int64_t ns,
+                                                           const StateFast* __restrict__ sfast, int64_t ns,
                                                            const double* __restrict__ qres, GridP gp,
                                                            double threshold, BoundP bp, int with_I,
                                                            const uint32_t* __restrict__ cand_t,
@@ -597,7 +643,6 @@ __global__ void __launch_bounds__(kThreadsI) k_lines_exact(const int32_t* __rest
                                                            unsigned* err) {
   constexpr int NW = kThreadsI / 32;
   __shared__ LinesConst kc;
-  __shared__ unsigned long long wmax[NW];
   if (threadIdx.x == 0) kc = lines_const(code, qhp, qres, gp, threshold, bp, with_I);
   __syncthreads();
   const LinesConst c = kc;
@@ -629,7 +674,11 @@ __global__ void __launch_bounds__(kThreadsI) k_lines_exact(const int32_t* __rest
           ab = cand_a[o];
         } else {
           t = (uint32_t)(ubase + j0 + lane);
-          ok = line_candidate(t, up, lo, Av, A32, ns, nullptr, c, bp, 0, &u, &l, &ab, &bad);
+          const LineIn x = line_load(t, up, lo, Av, A32);
+          ok = line_test(x, A32, ns, nullptr, c, bp, 0, &bad);
+          u = x.u;
+          l = x.l;
+          ab = x.ab;
         }
         if (ok) {
           const double A = A32 ? (double)__uint_as_float((unsigned)ab) : __longlong_as_double((long long)ab);
@@ -659,7 +708,7 @@ __global__ void __launch_bounds__(kThreadsI) k_lines_exact(const int32_t* __rest
             }
             if (keep) {
               double num, den;
-              line_value(bp.mode, bp.c2_Td, (double)fu.g, A, c.invQ, srec[l].y, srec[u].y, nu, &num, &den);
+              line_value(bp.mode, bp.c2_Td, (double)fu.g, A, c.invQ, fl.b, fu.b, nu, &num, &den);
               keep = fabs(num) >= threshold * den;
               if (keep) I = num / den;
             }
@@ -688,18 +737,13 @@ __global__ void __launch_bounds__(kThreadsI) k_lines_exact(const int32_t* __rest
       const unsigned long long v = __shfl_down_sync(0xffffffffu, mx, o);
       mx = v > mx ? v : mx;
     }
-    if (lane == 0) wmax[warp] = mx;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      unsigned long long m = 0;
-      for (int i = 0; i < NW; ++i) m = wmax[i] > m ? wmax[i] : m;
-      if (m) atomicMax(maxbits, m);
-    }
+    // one atomic per warp (no block barrier: a warp that finishes early frees its slot at once)
+    if (lane == 0 && mx) atomicMax(maxbits, mx);
   }
 }
 
 void launch_lines_compact(const pxc_transitions* tr, int64_t ns, const code_t* code, const QuantHdr* qh,
-                          const StateFast* sfast, const double2* srec,
+                          const StateFast* sfast,
                           const double* qres, const GridP& gp, double threshold, const BoundP& bp, int with_I,
                           uint32_t* cand_t, uint64_t* cand_ul, uint64_t* cand_a, uint32_t* ccount,
                           uint64_t* kstage, uint32_t* istage, double* Iv, uint32_t* ucount, int64_t nunit,
@@ -710,7 +754,7 @@ void launch_lines_compact(const pxc_transitions* tr, int64_t ns, const code_t* c
                                                    qres, gp, threshold, bp, with_I, cand_t, cand_ul, cand_a, ccount,
                                                    nunit, err);
   k_lines_exact<<<(unsigned)nblk, kThreadsI, 0, s>>>(tr->upper, tr->lower, tr->A, tr->A_is_f32, tr->n, code, qh,
-                                                     sfast, srec, ns, qres, gp, threshold, bp, with_I, cand_t, cand_ul,
+                                                     sfast, ns, qres, gp, threshold, bp, with_I, cand_t, cand_ul,
                                                      cand_a, ccount, kstage, istage, Iv, ucount, nunit, maxbits, err);
   note_launches(2);
 }
@@ -763,6 +807,68 @@ void launch_scan_counts(uint32_t* bcount, int64_t nblk, unsigned long long* tota
   note_launches(1);
 }
 
+
+// ------------------------------------------------------------------ non-zero lines of one temperature
+// Stable compaction of the sorted lines whose FP32 scaled intensity is non-zero (their records and
+// intensities), for the batched call: lines far below a list's strongest line round to zero at low
+// temperatures and add nothing to sigma.  Blocks of 256 threads take kUnitLines consecutive lines
+// each (count, exclusive scan of the counts, then writes in line order).
+__global__ void __launch_bounds__(256) k_nz_count(const float* __restrict__ Is, const unsigned long long* __restrict__ n_dev,
+                                                  uint32_t* __restrict__ bcount) {
+  __shared__ uint32_t wsum[8];
+  const int64_t n = (int64_t)*n_dev;
+  const int64_t base = (int64_t)blockIdx.x * kUnitLines;
+  uint32_t c = 0;
+  for (int r = 0; r < kUnitLines / 256; ++r) {
+    const int64_t j = base + r * 256 + threadIdx.x;
+    c += (j < n && Is[j] != 0.f) ? 1u : 0u;
+  }
+  c = warp_sum(c);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int i = 0; i < 8; ++i) t += wsum[i];
+    bcount[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_nz_write(const int4* __restrict__ pos, const float2* __restrict__ par,
+                                                  const float* __restrict__ Is, const unsigned long long* __restrict__ n_dev,
+                                                  const uint32_t* __restrict__ boff, int4* __restrict__ pos_c,
+                                                  float2* __restrict__ par_c, float* __restrict__ Is_c) {
+  __shared__ uint32_t wsum[8];
+  const int64_t n = (int64_t)*n_dev;
+  const int64_t base = (int64_t)blockIdx.x * kUnitLines;
+  if (base >= n) return;  // uniform per block
+  int64_t o = boff[blockIdx.x];
+  for (int r = 0; r < kUnitLines / 256; ++r) {
+    const int64_t j = base + r * 256 + threadIdx.x;
+    const float v = j < n ? Is[j] : 0.f;
+    uint32_t tot;
+    const uint32_t rank = block_rank(v != 0.f, wsum, &tot);
+    if (v != 0.f) {
+      pos_c[o + rank] = pos[j];
+      par_c[o + rank] = par[j];
+      Is_c[o + rank] = v;
+    }
+    o += tot;
+  }
+}
+
+void launch_compact_nonzero(const int4* pos, const float2* par, const float* Is, const unsigned long long* n_dev,
+                            int64_t n_max, uint32_t* bcount, unsigned long long* nnz_dev, int4* pos_c, float2* par_c,
+                            float* Is_c, cudaStream_t s) {
+  const int64_t nblk = (n_max + kUnitLines - 1) / kUnitLines;
+  if (nblk == 0) {
+    cudaMemsetAsync(nnz_dev, 0, sizeof(unsigned long long), s);
+    return;
+  }
+  k_nz_count<<<(unsigned)nblk, 256, 0, s>>>(Is, n_dev, bcount);
+  k_scan_counts<<<1, 1024, 0, s>>>(bcount, nblk, nnz_dev);
+  k_nz_write<<<(unsigned)nblk, 256, 0, s>>>(pos, par, Is, n_dev, bcount, pos_c, par_c, Is_c);
+  note_launches(3);
+}
 
 // ------------------------------------------------------------------ LSD radix sort, 8 passes of 8 bits
 // Pass: per-tile digit histogram -> per-digit exclusive scan over tiles -> stable scatter.
@@ -1125,7 +1231,8 @@ __global__ void __launch_bounds__(256) k_items_count(const int32_t* __restrict__
 __global__ void __launch_bounds__(256) k_items_emit(const int32_t* __restrict__ segr, int64_t nseg, int n_c,
                                                     int item_lines_max, const int32_t* __restrict__ seg_items,
                                                     Item* __restrict__ items, unsigned long long* __restrict__ counters,
-                                                    int64_t max_items, int64_t target_items, int64_t max_partial) {
+                                                    int64_t max_items, int64_t target_items, int64_t max_partial,
+                                                    const int32_t* __restrict__ cond_list) {
   const int L = item_lines_of(counters[CNT_ALL] * (unsigned long long)n_c, item_lines_max, target_items, max_partial);
   const int64_t ng = nseg * n_c;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1141,7 +1248,7 @@ __global__ void __launch_bounds__(256) k_items_emit(const int32_t* __restrict__ 
       const int64_t idx = (int64_t)first + k;
       if (idx >= max_items) break;  // sized on the host; never taken for calls that passed the capacity check
       Item it;
-      it.cond = (int32_t)(gi / nseg);
+      it.cond = cond_list ? cond_list[gi / nseg] : (int32_t)(gi / nseg);
       it.seg = (int32_t)s;
       it.begin = (int32_t)(f + (int64_t)k * L);
       const int64_t en = (int64_t)f + (int64_t)(k + 1) * L;
@@ -1158,7 +1265,7 @@ __global__ void __launch_bounds__(256) k_items_emit(const int32_t* __restrict__ 
 
 void launch_items(const int32_t* segr, int64_t nseg, int n_c, int item_lines, int32_t* seg_items, Item* items,
                   unsigned long long* counters, int64_t max_items, int64_t target_items, int64_t max_partial,
-                  cudaStream_t s) {
+                  const int32_t* cond_list, cudaStream_t s) {
   const int64_t ng = nseg * n_c;
   cudaMemsetAsync(counters + CNT_ALL, 0, sizeof(unsigned long long), s);
   auto blocks = [](int64_t n) { int64_t b = (n + 255) / 256; return (unsigned)(b < 1 ? 1 : (b > 148 * 8 ? 148 * 8 : b)); };
@@ -1167,7 +1274,7 @@ void launch_items(const int32_t* segr, int64_t nseg, int n_c, int item_lines, in
                                            reinterpret_cast<uint32_t*>(seg_items));
   k_scan_counts<<<1, 1024, 0, s>>>(reinterpret_cast<uint32_t*>(seg_items), ng, counters + CNT_ITEMS_RAW);
   k_items_emit<<<blocks(ng), 256, 0, s>>>(segr, nseg, n_c, item_lines, seg_items, items, counters, max_items,
-                                          target_items, max_partial);
+                                          target_items, max_partial, cond_list);
   note_launches(4);
 }
 

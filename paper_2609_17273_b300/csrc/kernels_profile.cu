@@ -325,10 +325,13 @@ __device__ __forceinline__ void line_constants(const int4 p4, const float2 pr, c
                                                LineC& c) {
   const int ic = p4.x;
   const float f = __int_as_float(p4.y);
-  c.pf = (float)((int64_t)ic - i0);
-  const int64_t lo = (int64_t)p4.z - i0, hi = (int64_t)p4.w - i0;
-  c.lo = (int)(lo < 0 ? 0 : lo);
-  c.hi = (int)(hi > SEG - 1 ? SEG - 1 : hi);
+  // grid indices fit in 32 bits (the host caps the grid below 2^31 - 2 segments), so the
+  // segment offsets are 32-bit integer arithmetic (a 64-bit conversion would use the FP64 pipe)
+  const int i0i = (int)i0;
+  c.pf = (float)(ic - i0i);
+  const int lo = p4.z - i0i, hi = p4.w - i0i;
+  c.lo = lo < 0 ? 0 : lo;
+  c.hi = hi > SEG - 1 ? SEG - 1 : hi;
   const float cen = c.pf + f;  // line centre in grid steps from the segment start
   float reach = 0.f;           // half-width (grid steps) of the zone needing the general path
   if (is_binned(KIND)) {
@@ -473,20 +476,41 @@ __device__ __forceinline__ int line_class(const LineC& c, int a) {
 // sigma^2, the denominator by sigma^4), so the value is unchanged and the scaled denominators lie
 // in [~1, 2^52] when max |x| <= 2^12 x_ref.  Returns false (the line then takes the masked
 // single-line path) when the warp spans a wider range of |x| than that.
+//
+// Where |z|^2 = x^2 + y^2 >= kLorentzR2 at every point of the warp, the line's far wing is taken in
+// its Lorentzian limit K / (x^2 + y^2) instead: the region-I value is
+//   K (u + 1) / (u^2 + e) = (K / |z|^2) (|z|^4 + |z|^2 / 2) / (|z|^4 - x^2 + y^2 + 1/4)
+//                         = (K / |z|^2) (1 + (3 x^2 - y^2) / (2 |z|^4) + O(|z|^-4)),
+// so the limit is within 1.5 / |z|^2 <= 3e-5 of it (relative).  Such a line is marked by d < 0 and
+// carries B1 = sigma^2 y^2 (its scaled denominator is x'^2 + B1); two of them cost eight FP32
+// instructions and one reciprocal per point, against twelve and one for two region-I lines.
+#ifndef PXC_LORENTZ_R2
+#define PXC_LORENTZ_R2 5e4f
+#endif
+constexpr float kLorentzR2 = PXC_LORENTZ_R2;
+
 template <int WPTS>
 __device__ __forceinline__ bool scale_for_pairs(LineC& c, int wbase) {
   const float wlo = (float)wbase, whi = (float)(wbase + WPTS - 1);
   const float dmin = fmaxf(0.f, fmaxf(c.cen - whi, wlo - c.cen));
   const float dmax = fmaxf(fabsf(c.cen - wlo), fabsf(c.cen - whi));
-  const float xref = fmaxf(dmin * c.step, c.y);
+  const float xm = dmin * c.step;
+  const float xref = fmaxf(xm, c.y);
   if (!(xref > 0.f) || !(dmax * c.step <= 4096.f * xref)) return false;
+  const bool lorentz = fmaf(xm, xm, c.y * c.y) >= kLorentzR2;
   const int ex = (__float_as_int(xref) >> 23) & 0xff;  // xref = m 2^(ex - 127), 1 <= m < 2
   const float sg = __int_as_float((254 - ex) << 23);   // 2^(127 - ex)
   const float sg2 = sg * sg;
   c.a *= sg;
   c.b *= sg;
-  c.B1 *= sg2;
-  c.d *= sg2 * sg2;
+  if (lorentz) {
+    const float ys = c.y * sg;
+    c.B1 = ys * ys;
+    c.d = -1.f;
+  } else {
+    c.B1 *= sg2;
+    c.d *= sg2 * sg2;
+  }
   c.KA = c.K * (sg2 * sg2);
   c.K *= sg2;
   return true;
@@ -503,6 +527,15 @@ __device__ __forceinline__ void eval_fast(const LineC& c, const float* lk, float
     // reciprocal per point); no point of this warp is near the centre, so x = x(lane 0) + m step
     // keeps full relative accuracy
     const float KA = c.KA;  // K sigma^4, the rescaled numerator's constant term
+    if (f0.w < 0.f) {
+      // Lorentzian limit (see scale_for_pairs)
+#pragma unroll
+      for (int k = 0; k < PTS; ++k) {
+        const float x = fmaf(lk[k], f0.y, f0.x);
+        acc[k] = fmaf(K, frcp(fmaf(x, x, f0.z)), acc[k]);
+      }
+      return;
+    }
 #pragma unroll
     for (int k = 0; k < PTS; ++k) {
       const float x = fmaf(lk[k], f0.y, f0.x);
@@ -534,6 +567,31 @@ __device__ __forceinline__ void eval_fast2(const LineC& c, const LineC& e, const
   if (KIND == PXC_VOIGT) {
     const float4 a0 = *reinterpret_cast<const float4*>(&c.a), a1 = *reinterpret_cast<const float4*>(&c.K);
     const float4 b0 = *reinterpret_cast<const float4*>(&e.a), b1 = *reinterpret_cast<const float4*>(&e.K);
+    const bool lc = a0.w < 0.f, le = b0.w < 0.f;  // Lorentzian limits (the same for every lane)
+    if (lc && le) {
+      // K_c / d_c + K_e / d_e, d = x'^2 + sigma^2 y^2 (four FP32 operations and half a MUFU per evaluation)
+#pragma unroll
+      for (int k = 0; k < PTS; ++k) {
+        const float x = fmaf(lk[k], a0.y, a0.x), y = fmaf(lk[k], b0.y, b0.x);
+        const float du = fmaf(x, x, a0.z), dv = fmaf(y, y, b0.z);
+        acc[k] = fmaf(fmaf(b1.x, du, a1.x * dv), frcp(du * dv), acc[k]);
+      }
+      return;
+    }
+    if (lc || le) {
+      // one region-I line (r) and one in the Lorentzian limit (q)
+      const float4 r0 = lc ? b0 : a0, r1 = lc ? b1 : a1, q0 = lc ? a0 : b0;
+      const float Kq = lc ? a1.x : b1.x;
+#pragma unroll
+      for (int k = 0; k < PTS; ++k) {
+        const float x = fmaf(lk[k], r0.y, r0.x), y = fmaf(lk[k], q0.y, q0.x);
+        const float u = fmaf(x, x, r0.z);
+        const float du = fmaf(u, u, r0.w), dv = fmaf(y, y, q0.z);
+        const float nu = fmaf(u, r1.x, r1.y);
+        acc[k] = fmaf(fmaf(Kq, du, nu * dv), frcp(du * dv), acc[k]);
+      }
+      return;
+    }
 #pragma unroll
     for (int k = 0; k < PTS; ++k) {
       const float x = fmaf(lk[k], a0.y, a0.x), y = fmaf(lk[k], b0.y, b0.x);
@@ -741,7 +799,10 @@ __device__ __forceinline__ void eval_slow(const LineC& c, int wbase, int lane, c
 // fast lines from the front, the others from the back.  The last warp to finish reading a
 // stage buffer re-arms it with the copy kNB stages ahead, so warps drift apart by up to
 // kNB - 1 stages instead of waiting for each other at every stage.
-constexpr int kNB = 3;
+#ifndef PXC_STAGE_BUFFERS
+#define PXC_STAGE_BUFFERS 3
+#endif
+constexpr int kNB = PXC_STAGE_BUFFERS;
 
 template <int THREADS, int SL>
 constexpr size_t profile_smem() {
@@ -825,11 +886,15 @@ __global__ void __launch_bounds__(THREADS, MINB) k_profile(const ProfP p) {
       for (int r = 0; r < SL / 32; ++r) {
         const int j = lane + 32 * r;
         const int64_t J = (int64_t)j0 + (int64_t)st * SL + j;
+        const float is = reinterpret_cast<const float*>(src + SL * 24)[j];
+        const bool live = is != 0.f && J >= item.begin && J < item.end;
+        // lines whose FP32 scaled intensity is zero add nothing: a round of 32 without a live line
+        // builds no constants (lists far below their strongest line are mostly such lines)
+        if (!__any_sync(0xffffffffu, live)) continue;
         const int4 p4 = reinterpret_cast<const int4*>(src)[j];
         const float2 pr = reinterpret_cast<const float2*>(src + SL * 16)[j];
-        const float is = reinterpret_cast<const float*>(src + SL * 24)[j];
         LineC c;
-        line_constants<KIND, SEG>(p4, pr, is, cd, i0, wbase, dnu_f, nu_min_f, J >= item.begin && J < item.end, c);
+        line_constants<KIND, SEG>(p4, pr, is, cd, i0, wbase, dnu_f, nu_min_f, live, c);
         int cls = line_class<KIND, WPTS>(c, wbase);
         if (KIND == PXC_VOIGT && cls == 1 && !scale_for_pairs<WPTS>(c, wbase)) cls = 2;
         c.masks = cls;
@@ -1103,24 +1168,35 @@ void launch_profile_wl(const ProfP& p, int64_t max_items, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ adjoint
-// One warp per sorted line: the lanes stride over the line's window, recompute the
-// profile and its width derivatives at each point and accumulate them against
-// w = dL/dsigma_s.  With G = sum w f, Da = sum w df/dalpha, Dg = sum w df/dgamma
-// (times the scaled intensity I_s) the chain rule gives
+// One warp per batch of 32 consecutive sorted lines.  Lane q loads line q and builds its widths;
+// for each line of the batch in turn the lanes stride over its window (the line's values broadcast
+// by shuffles), recompute the profile and its width derivatives at each point and accumulate them
+// against w = dL/dsigma_s; a butterfly sum leaves the totals in every lane and lane q keeps line
+// q's.  With G = sum w f, Da = sum w df/dalpha, Dg = sum w df/dgamma (times the scaled intensity
+// I_s) the chain rule gives
 //   dL/dA_l = I_s G / A_l,  dL/dgamma_ref_l = I_s (T_ref/T)^n P Dg,
-//   per-line shares of dL/dT (T_rot), dL/dT_vib and dL/dP (FP64, reduced in a fixed order).
+//   per-line shares of dL/dT (T_rot), dL/dT_vib and dL/dP (FP64, reduced in a fixed order),
+// evaluated on all 32 lanes at once (one line each).
 // Voigt: f = (c/sqrt(pi)) Re w(z), z = (x + i gamma) c, c = sqrt(ln2)/alpha, with
 //   df/dgamma = -(c^2/sqrt(pi)) Im w'(z),  df/dalpha = -(c/(alpha sqrt(pi))) (Re w + Re(z w'(z))).
 template <int KIND>
 __global__ void __launch_bounds__(256) k_adjoint(const AdjP p) {
   const int lane = threadIdx.x & 31;
   const int64_t n = (int64_t)*p.n_dev;
+  const int64_t nbatch = (n + 31) >> 5;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const float dnu_f = (float)p.dnu;
-  for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < n; j += warps) {
-    const int4 p4 = p.pos[j];
-    const float2 pr = p.par[j];
-    const float is = p.Is[j];
+  for (int64_t bt = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; bt < nbatch; bt += warps) {
+    const int64_t j = bt * 32 + lane;
+    const bool valid = j < n;
+    int4 p4 = make_int4(0, 0, 0, -1);
+    float2 pr = make_float2(0.f, 0.f);
+    float is = 0.f;
+    if (valid) {
+      p4 = p.pos[j];
+      pr = p.par[j];
+      is = p.Is[j];
+    }
     const int ic = p4.x;
     const float f = __int_as_float(p4.y);
     const float nu_f = (float)(p.nu_min + ((double)ic + (double)f) * p.dnu);
@@ -1128,93 +1204,105 @@ __global__ void __launch_bounds__(256) k_adjoint(const AdjP p) {
     const float gfac = exp2f(pr.y * p.cond.log2_tratio) * p.cond.P_f;   // dgamma/dgamma_ref
     const float gam = KIND == PXC_LORENTZ ? fmaxf(pr.x * gfac, kGammaMin) : KIND == PXC_VOIGT ? pr.x * gfac : 0.f;
     const float cc = kSqrtLn2 / alpha;
-    float g0 = 0.f, ga = 0.f, gg = 0.f;
-    if (is != 0.f) {
-      for (int i = p4.z + lane; i <= p4.w; i += 32) {
+    float g0 = 0.f, ga = 0.f, gg = 0.f;  // lane q: the sums of line q
+    for (int q = 0; q < 32; ++q) {
+      if (__shfl_sync(0xffffffffu, is, q) == 0.f) continue;  // no contribution to sigma (uniform)
+      const int icq = __shfl_sync(0xffffffffu, ic, q);
+      const int loq = __shfl_sync(0xffffffffu, p4.z, q), hiq = __shfl_sync(0xffffffffu, p4.w, q);
+      const float fq = __shfl_sync(0xffffffffu, f, q);
+      const float ccq = __shfl_sync(0xffffffffu, cc, q), gamq = __shfl_sync(0xffffffffu, gam, q);
+      float s0 = 0.f, sa = 0.f, sg = 0.f;
+      for (int i = loq + lane; i <= hiq; i += 32) {
         const float wi = p.w[i];
-        const float x = ((float)(i - ic) - f) * dnu_f;
+        const float x = ((float)(i - icq) - fq) * dnu_f;
         if (KIND == PXC_VOIGT) {
-          const float X = x * cc, Y = gam * cc;
+          const float X = x * ccq, Y = gamq * ccq;
           cplx w, dw;
           w4_full(X, Y, &w, &dw);
-          g0 = fmaf(wi, w.r, g0);
-          gg = fmaf(wi, dw.i, gg);
-          ga = fmaf(wi, w.r + (X * dw.r - Y * dw.i), ga);
+          s0 = fmaf(wi, w.r, s0);
+          sg = fmaf(wi, dw.i, sg);
+          sa = fmaf(wi, w.r + (X * dw.r - Y * dw.i), sa);
         } else if (KIND == PXC_LORENTZ) {
-          const float x2 = x * x, g2 = gam * gam;
+          const float x2 = x * x, g2 = gamq * gamq;
           const float d = 1.f / (x2 + g2);
-          g0 = fmaf(wi, d, g0);
-          gg = fmaf(wi, (x2 - g2) * d * d, gg);
+          s0 = fmaf(wi, d, s0);
+          sg = fmaf(wi, (x2 - g2) * d * d, sg);
         } else {
-          const float X = x * cc;
+          const float X = x * ccq;
           const float e = expf(-X * X);
-          g0 = fmaf(wi, e, g0);
-          ga = fmaf(wi, e * X * X, ga);
+          s0 = fmaf(wi, e, s0);
+          sa = fmaf(wi, e * X * X, sa);
         }
       }
-    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      g0 += __shfl_down_sync(0xffffffffu, g0, o);
-      ga += __shfl_down_sync(0xffffffffu, ga, o);
-      gg += __shfl_down_sync(0xffffffffu, gg, o);
+      for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        sa += __shfl_xor_sync(0xffffffffu, sa, o);
+        sg += __shfl_xor_sync(0xffffffffu, sg, o);
+      }
+      if (lane == q) {
+        g0 = s0;
+        ga = sa;
+        gg = sg;
+      }
     }
-    if (lane == 0 && is == 0.f) {
+    if (!valid) continue;
+    if (is == 0.f) {
       // zero scaled intensity: no contribution to sigma, hence none to any gradient
       p.lineT[j] = 0.0;
       p.lineTv[j] = 0.0;
       p.lineP[j] = 0.0;
-    } else if (lane == 0) {
-      const uint32_t t = p.sidx[j];
-      double G = 0.0, Da = 0.0, Dg = 0.0;
-      const double ccd = cc, ad = alpha, spi = 1.7724538509055160273;
-      if (KIND == PXC_VOIGT) {
-        G = ccd / spi * g0;
-        Dg = -(ccd * ccd / spi) * gg;
-        Da = -(ccd / (ad * spi)) * ga;
-      } else if (KIND == PXC_LORENTZ) {
-        G = (double)gam / kPi * g0;
-        Dg = gg / kPi;
-      } else {
-        G = ccd / spi * g0;
-        Da = ccd / spi * (-(double)g0 + 2.0 * ga) / ad;
-      }
-      const double I = is;
-      const double A = p.sA[j];
-      if (p.dA) p.dA[t] = (float)(I * G / A);
-      if (p.dgref) p.dgref[t] = (float)(I * (double)gfac * Dg);
-      const int32_t u = p.su[j], l = p.sl[j];
-      const double Eu = p.srec[u].x, El = p.srec[l].x;
-      const double c2 = p.c2, T = p.T;
-      const double Q = p.qres[0], dQ = p.qres[1], dQv = p.qres[2];
-      double dlnT, dlnTv = 0.0;
-      if (p.T_vib > 0.0) {
-        const double evl = p.E_vib[l], evu = p.E_vib[u];
-        const double erl = El - evl, eru = Eu - evu;
-        const double nv = evu - evl, nr = eru - erl;
-        const double X = c2 * (nv / p.T_vib + nr / T);
-        const double st = 1.0 / expm1(X);
-        dlnT = c2 * erl / (T * T) - c2 * nr / (T * T) * st - dQ / Q;
-        dlnTv = c2 * evl / (p.T_vib * p.T_vib) - c2 * nv / (p.T_vib * p.T_vib) * st - dQv / Q;
-      } else {
-        const double nu = Eu - El;
-        const double st = 1.0 / expm1(c2 * nu / T);
-        dlnT = c2 * El / (T * T) - c2 * nu / (T * T) * st - dQ / Q;
-      }
-      const bool dop = KIND == PXC_GAUSS_DOPPLER || KIND == PXC_VOIGT;
-      const bool pres = KIND == PXC_LORENTZ || KIND == PXC_VOIGT;
-      const double dadT = dop ? ad / (2.0 * T) : 0.0;
-      const double dgdT = pres ? -(double)pr.y * (double)gam / T : 0.0;
-      const double dgdP = pres ? (double)gam / p.P : 0.0;
-      p.lineT[j] = I * (dlnT * G + dadT * Da + dgdT * Dg);
-      p.lineTv[j] = I * dlnTv * G;
-      p.lineP[j] = I * dgdP * Dg;
+      continue;
     }
+    const uint32_t t = p.sidx[j];
+    double G = 0.0, Da = 0.0, Dg = 0.0;
+    const double ccd = cc, ad = alpha, spi = 1.7724538509055160273;
+    if (KIND == PXC_VOIGT) {
+      G = ccd / spi * g0;
+      Dg = -(ccd * ccd / spi) * gg;
+      Da = -(ccd / (ad * spi)) * ga;
+    } else if (KIND == PXC_LORENTZ) {
+      G = (double)gam / kPi * g0;
+      Dg = gg / kPi;
+    } else {
+      G = ccd / spi * g0;
+      Da = ccd / spi * (-(double)g0 + 2.0 * ga) / ad;
+    }
+    const double I = is;
+    const double A = p.sA[j];
+    if (p.dA) p.dA[t] = (float)(I * G / A);
+    if (p.dgref) p.dgref[t] = (float)(I * (double)gfac * Dg);
+    const int32_t u = p.su[j], l = p.sl[j];
+    const double Eu = p.srec[u].x, El = p.srec[l].x;
+    const double c2 = p.c2, T = p.T;
+    const double Q = p.qres[0], dQ = p.qres[1], dQv = p.qres[2];
+    double dlnT, dlnTv = 0.0;
+    if (p.T_vib > 0.0) {
+      const double evl = p.E_vib[l], evu = p.E_vib[u];
+      const double erl = El - evl, eru = Eu - evu;
+      const double nv = evu - evl, nr = eru - erl;
+      const double X = c2 * (nv / p.T_vib + nr / T);
+      const double st = 1.0 / expm1(X);
+      dlnT = c2 * erl / (T * T) - c2 * nr / (T * T) * st - dQ / Q;
+      dlnTv = c2 * evl / (p.T_vib * p.T_vib) - c2 * nv / (p.T_vib * p.T_vib) * st - dQv / Q;
+    } else {
+      const double nu = Eu - El;
+      const double st = 1.0 / expm1(c2 * nu / T);
+      dlnT = c2 * El / (T * T) - c2 * nu / (T * T) * st - dQ / Q;
+    }
+    const bool dop = KIND == PXC_GAUSS_DOPPLER || KIND == PXC_VOIGT;
+    const bool pres = KIND == PXC_LORENTZ || KIND == PXC_VOIGT;
+    const double dadT = dop ? ad / (2.0 * T) : 0.0;
+    const double dgdT = pres ? -(double)pr.y * (double)gam / T : 0.0;
+    const double dgdP = pres ? (double)gam / p.P : 0.0;
+    p.lineT[j] = I * (dlnT * G + dadT * Da + dgdT * Dg);
+    p.lineTv[j] = I * dlnTv * G;
+    p.lineP[j] = I * dgdP * Dg;
   }
 }
 
 void launch_adjoint(const AdjP& p, cudaStream_t s) {
-  int64_t blocks = (p.n_max * 32 + 255) / 256;
+  int64_t blocks = ((p.n_max + 31) / 32 * 32 + 255) / 256;
   if (blocks > 148 * 8) blocks = 148 * 8;
   if (blocks < 1) blocks = 1;
   switch (p.kind) {
@@ -1226,39 +1314,78 @@ void launch_adjoint(const AdjP& p, cudaStream_t s) {
   note_launches(1);
 }
 
-// Fixed-order FP64 reduction of the per-line scalar shares (one CTA).
-__global__ void k_adjoint_reduce(const double* __restrict__ a, const double* __restrict__ b,
-                                 const double* __restrict__ c, const unsigned long long* __restrict__ n_dev,
-                                 double* oa, double* ob, double* oc) {
-  __shared__ double r[3][1024];
-  const int64_t n = (int64_t)*n_dev;
-  int64_t per = (n + blockDim.x - 1) / blockDim.x;
-  int64_t lo = threadIdx.x * per, hi = lo + per < n ? lo + per : n;
-  double sa = 0, sb = 0, sc = 0;
-  for (int64_t i = lo; i < hi; ++i) { sa += a[i]; sb += b[i]; sc += c[i]; }
-  r[0][threadIdx.x] = sa; r[1][threadIdx.x] = sb; r[2][threadIdx.x] = sc;
+// Fixed-order FP64 reduction of the per-line scalar shares in two launches: kRedBlocks CTAs each
+// sum one contiguous range (thread t takes every kRedThreads-th element of it, then a fixed tree),
+// and one CTA sums the per-CTA totals the same way.  The order depends only on the line count.
+constexpr int kRedBlocks = 296, kRedThreads = 256;
+
+__device__ __forceinline__ void tree3(double (*r)[kRedThreads], double* sa, double* sb, double* sc) {
+  const int t = threadIdx.x;
+  r[0][t] = *sa;
+  r[1][t] = *sb;
+  r[2][t] = *sc;
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) {
-      r[0][threadIdx.x] += r[0][threadIdx.x + o];
-      r[1][threadIdx.x] += r[1][threadIdx.x + o];
-      r[2][threadIdx.x] += r[2][threadIdx.x + o];
+  for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+    if (t < o) {
+      r[0][t] += r[0][t + o];
+      r[1][t] += r[1][t + o];
+      r[2][t] += r[2][t + o];
     }
     __syncthreads();
   }
+  *sa = r[0][0];
+  *sb = r[1][0];
+  *sc = r[2][0];
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_adjoint_reduce(const double* __restrict__ a,
+                                                                const double* __restrict__ b,
+                                                                const double* __restrict__ c,
+                                                                const unsigned long long* __restrict__ n_dev,
+                                                                double* __restrict__ part) {
+  __shared__ double r[3][kRedThreads];
+  const int64_t n = (int64_t)*n_dev;
+  const int64_t per = (n + kRedBlocks - 1) / kRedBlocks;
+  const int64_t lo = (int64_t)blockIdx.x * per, hi = lo + per < n ? lo + per : n;
+  double sa = 0.0, sb = 0.0, sc = 0.0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += kRedThreads) {
+    sa += a[i];
+    sb += b[i];
+    sc += c[i];
+  }
+  tree3(r, &sa, &sb, &sc);
   if (threadIdx.x == 0) {
-    if (oa) *oa = r[0][0];
-    if (ob) *ob = r[1][0];
-    if (oc) *oc = r[2][0];
+    part[blockIdx.x] = sa;
+    part[kRedBlocks + blockIdx.x] = sb;
+    part[2 * kRedBlocks + blockIdx.x] = sc;
   }
 }
 
+__global__ void __launch_bounds__(kRedThreads) k_adjoint_reduce_final(const double* __restrict__ part, double* oa,
+                                                                      double* ob, double* oc) {
+  __shared__ double r[3][kRedThreads];
+  double sa = 0.0, sb = 0.0, sc = 0.0;
+  for (int i = threadIdx.x; i < kRedBlocks; i += kRedThreads) {
+    sa += part[i];
+    sb += part[kRedBlocks + i];
+    sc += part[2 * kRedBlocks + i];
+  }
+  tree3(r, &sa, &sb, &sc);
+  if (threadIdx.x == 0) {
+    if (oa) *oa = sa;
+    if (ob) *ob = sb;
+    if (oc) *oc = sc;
+  }
+}
+
+size_t adjoint_reduce_scratch_bytes() { return (size_t)3 * kRedBlocks * sizeof(double); }
+
 void launch_adjoint_reduce(const double* lineT, const double* lineTv, const double* lineP,
-                           const unsigned long long* n_dev, int64_t n_max, double* outT, double* outTv,
+                           const unsigned long long* n_dev, double* scratch, double* outT, double* outTv,
                            double* outP, cudaStream_t s) {
-  (void)n_max;
-  k_adjoint_reduce<<<1, 1024, 0, s>>>(lineT, lineTv, lineP, n_dev, outT, outTv, outP);
-  note_launches(1);
+  k_adjoint_reduce<<<kRedBlocks, kRedThreads, 0, s>>>(lineT, lineTv, lineP, n_dev, scratch);
+  k_adjoint_reduce_final<<<1, kRedThreads, 0, s>>>(scratch, outT, outTv, outP);
+  note_launches(2);
 }
 
 }  // namespace pxc

@@ -37,7 +37,8 @@ size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
   size_t err, counters, qpart, qres, slots, cond, srec, sfast, key, Iv, bcount, skey0, skey1, sidx0, sidx1, rcount, pos,
-      par, Is, su, sl, sA, sI, segr, seg_items, items, partial, kexp, maxbits, params, code, qwords, total;
+      par, Is, su, sl, sA, sI, segr, seg_items, items, partial, kexp, maxbits, params, code, qwords, pos_c, par_c,
+      Is_c, condlist, total;
   int64_t max_seg, max_items, max_slots, nblk_I, nblk_sort, max_cond, is_stride;
   int64_t partial_floats;  // partial-row buffer; a tile of S points has partial_floats / S rows
 };
@@ -94,6 +95,13 @@ Layout make_layout(const pxc_capacity& c) {
   L.params = take(4096);
   L.code = take(code_bytes(std::max<int64_t>(c.max_states, 1)));
   L.qwords = take(kQuantWords * 8 + sizeof(QuantHdr));
+  // batched calls: the lines of one temperature with non-zero scaled intensity, and the
+  // conditions grouped by temperature
+  const size_t nzl = L.max_cond > 1 ? (size_t)(ml + kPad) : 0;
+  L.pos_c = take(nzl * 16);
+  L.par_c = take(nzl * 8);
+  L.Is_c = take(nzl * 4);
+  L.condlist = take((size_t)L.max_cond * 4);
   L.total = o;
   return L;
 }
@@ -350,7 +358,7 @@ pxc_status front_plain(pxc_workspace* ws, const pxc_states* st, const pxc_transi
   tmark(ws, 0, true, s);
   BoundP bp = make_bound(ws, st, c, threshold);
   launch_lines_compact(tr, st->n, at<code_t>(ws, L.code), qhdr(ws), at<StateFast>(ws, L.sfast),
-                       at<double2>(ws, L.srec), at<double>(ws, L.qres), gp, threshold, bp, 1, CAND_BUFFERS(ws, L),
+                       at<double>(ws, L.qres), gp, threshold, bp, 1, CAND_BUFFERS(ws, L),
                        at<uint64_t>(ws, L.key), at<uint32_t>(ws, L.sidx1), at<double>(ws, L.Iv),
                        at<uint32_t>(ws, L.bcount), nunit, at<unsigned long long>(ws, L.maxbits), ws->err, s);
   tmark(ws, 0, false, s);
@@ -600,6 +608,33 @@ pxc_status pxc_line_intensities(pxc_workspace* ws, const pxc_states* st, const p
 
 namespace {
 
+// Profile-kernel arguments over the sorted list of the call (all temperature slots' intensities).
+ProfP profile_params(pxc_workspace* ws, const pxc_profile_args* pa, const pxc_grid* grid, const CondDev* dcond,
+                     float* sigma_out, long long wait_limit) {
+  const Layout& L = X(ws)->L;
+  ProfP p{};
+  p.pos = at<int4>(ws, L.pos);
+  p.par = at<float2>(ws, L.par);
+  p.Is = at<float>(ws, L.Is);
+  p.is_stride = L.is_stride;
+  p.cond = dcond;
+  p.items = at<Item>(ws, L.items);
+  p.n_items = at<unsigned long long>(ws, L.counters) + CNT_ITEMS;
+  p.queue = at<unsigned long long>(ws, L.counters) + CNT_QUEUE;
+  p.sigma = sigma_out;
+  p.partial = at<float>(ws, L.partial);
+  p.n_grid = grid->n;
+  p.nu_min = grid->nu_min;
+  p.dnu = grid->dnu;
+  p.accumulate = ws->accumulate;
+  p.kind = pa->kind;
+  p.err = ws->err;
+  p.spin_limit = wait_limit;
+  p.drain_limit = kDefaultWaitLimit;  // copies in flight always land; this bound is never the one reached
+  p.wl_unit = grid->wl_unit;
+  return p;
+}
+
 pxc_status cross_section_direct(pxc_workspace* ws, const pxc_states* st, const pxc_transitions* tr,
                                 const pxc_condition* c, int32_t n_c, const pxc_grid* grid,
                                 const pxc_profile_args* pa, double threshold, float* sigma_out,
@@ -666,7 +701,7 @@ pxc_status cross_section_direct(pxc_workspace* ws, const pxc_states* st, const p
     const int64_t nunit = (tr->n + kUnitLines - 1) / kUnitLines;
     BoundP bp = make_bound(ws, st, c[0], 0.0);
     launch_lines_compact(tr, st->n, at<code_t>(ws, L.code), qhdr(ws), at<StateFast>(ws, L.sfast),
-                         at<double2>(ws, L.srec), at<double>(ws, L.qres), gp, 0.0, bp, 0, CAND_BUFFERS(ws, L),
+                         at<double>(ws, L.qres), gp, 0.0, bp, 0, CAND_BUFFERS(ws, L),
                          at<uint64_t>(ws, L.key), idxs[1], nullptr, at<uint32_t>(ws, L.bcount), nunit, nullptr,
                          ws->err, s);
     if (nunit) launch_scan_counts(at<uint32_t>(ws, L.bcount), nunit, cnt + CNT_KEPT, s);
@@ -675,6 +710,19 @@ pxc_status cross_section_direct(pxc_workspace* ws, const pxc_states* st, const p
     launch_prepare(keys[0], idxs[0], cnt + CNT_KEPT, tr->n, gp, pa->gamma_ref, pa->n_T, nullptr, kexp,
                    at<int4>(ws, L.pos), at<float2>(ws, L.par), nullptr, tr, at<int32_t>(ws, L.su),
                    at<int32_t>(ws, L.sl), at<double>(ws, L.sA), nullptr, cnt, s);
+    // conditions grouped by temperature slot (wavenumber grids: one profile launch per slot over
+    // that slot's lines with non-zero scaled intensity)
+    std::vector<int32_t> order;
+    std::vector<int> first(slots.size() + 1, 0);
+    for (size_t k = 0; k < slots.size(); ++k) {
+      first[k] = (int)order.size();
+      for (int i = 0; i < n_c; ++i)
+        if (slot_of[i] == (int)k) order.push_back(i);
+    }
+    first[slots.size()] = (int)order.size();
+    int32_t* condlist = at<int32_t>(ws, L.condlist);
+    if (!wl && (r = upload(ws, condlist, order.data(), sizeof(int32_t) * order.size(), s))) return r;
+    const int ctas_b = profile_ctas(ws, pa->kind, tile);
     for (size_t k = 0; k < slots.size(); ++k) {
       if (k) run_boltzmann(ws, st, slots[k], (int)k, s, false);
       cudaMemsetAsync(at<unsigned long long>(ws, L.maxbits) + k, 0, 8, s);
@@ -683,37 +731,41 @@ pxc_status cross_section_direct(pxc_workspace* ws, const pxc_states* st, const p
                               make_bound(ws, st, slots[k], threshold), threshold, at<double>(ws, L.sI),
                               at<unsigned long long>(ws, L.maxbits) + k, s);
       launch_exponent(at<unsigned long long>(ws, L.maxbits) + k, kexp + 2 * k, nullptr, 0, nullptr, 0, s);
-      launch_scale(at<double>(ws, L.sI), cnt + CNT_KEPT, tr->n, kexp + 2 * k,
-                   at<float>(ws, L.Is) + (int64_t)k * L.is_stride, cnt, s);
+      float* Is_k = at<float>(ws, L.Is) + (int64_t)k * L.is_stride;
+      launch_scale(at<double>(ws, L.sI), cnt + CNT_KEPT, tr->n, kexp + 2 * k, Is_k, cnt, s);
+      if (wl) continue;
+      launch_compact_nonzero(at<int4>(ws, L.pos), at<float2>(ws, L.par), Is_k, cnt + CNT_KEPT, tr->n,
+                             at<uint32_t>(ws, L.bcount), cnt + CNT_SLOT_NZ, at<int4>(ws, L.pos_c),
+                             at<float2>(ws, L.par_c), at<float>(ws, L.Is_c), s);
+      launch_segments(at<int4>(ws, L.pos_c), cnt + CNT_SLOT_NZ, nseg, seg, at<int32_t>(ws, L.segr), s);
+      launch_items(at<int32_t>(ws, L.segr), nseg, first[k + 1] - first[k], INT32_MAX / 2,
+                   at<int32_t>(ws, L.seg_items), at<Item>(ws, L.items), cnt, L.max_items, 0ll, max_partial,
+                   condlist + first[k], s);
+      ProfP p = profile_params(ws, pa, grid, dcond, sigma_out, x->wait_limit);
+      p.pos = at<int4>(ws, L.pos_c);
+      p.par = at<float2>(ws, L.par_c);
+      p.Is = at<float>(ws, L.Is_c);
+      p.is_stride = 0;
+      tmark(ws, 2, true, s);
+      launch_profile(p, tile, ctas_b, s);
+      tmark(ws, 2, false, s);
     }
     for (int i = 0; i < n_c; ++i)
       cudaMemcpyAsync(sigma_exp_out + i, kexp + 2 * slot_of[i], 4, cudaMemcpyDeviceToDevice, s);
+    if (!wl) {
+      x->last_nseg = nseg;
+      x->last_seg = seg;
+      x->last_tile = tile;
+      ws->last_nc = n_c;
+      return cuda_check("cross_section");
+    }
   }
   const int ctas = profile_ctas(ws, pa->kind, tile);
   const bool split = n_c == 1 && !wl;  // only single-condition wavenumber calls split segments
   launch_segments(at<int4>(ws, L.pos), cnt + CNT_KEPT, nseg, seg, at<int32_t>(ws, L.segr), s);
   launch_items(at<int32_t>(ws, L.segr), nseg, n_c, split ? kItemLines : INT32_MAX / 2, at<int32_t>(ws, L.seg_items),
-               at<Item>(ws, L.items), cnt, L.max_items, split ? 16ll * ctas : 0ll, max_partial, s);
-  ProfP p{};
-  p.pos = at<int4>(ws, L.pos);
-  p.par = at<float2>(ws, L.par);
-  p.Is = at<float>(ws, L.Is);
-  p.is_stride = L.is_stride;
-  p.cond = dcond;
-  p.items = at<Item>(ws, L.items);
-  p.n_items = cnt + CNT_ITEMS;
-  p.queue = cnt + CNT_QUEUE;
-  p.sigma = sigma_out;
-  p.partial = at<float>(ws, L.partial);
-  p.n_grid = grid->n;
-  p.nu_min = grid->nu_min;
-  p.dnu = grid->dnu;
-  p.accumulate = ws->accumulate;
-  p.kind = pa->kind;
-  p.err = ws->err;
-  p.spin_limit = x->wait_limit;
-  p.drain_limit = kDefaultWaitLimit;  // copies in flight always land; this bound is never the one reached
-  p.wl_unit = grid->wl_unit;
+               at<Item>(ws, L.items), cnt, L.max_items, split ? 16ll * ctas : 0ll, max_partial, nullptr, s);
+  ProfP p = profile_params(ws, pa, grid, dcond, sigma_out, x->wait_limit);
   tmark(ws, 2, true, s);
   if (wl) launch_profile_wl(p, (int64_t)n_c * nseg, s);
   else launch_profile(p, tile, ctas, s);
@@ -913,7 +965,10 @@ pxc_status pxc_cross_section_backward(pxc_workspace* ws, const pxc_states* st, c
   p.lineTv = at<double>(ws, L.Iv);
   p.lineP = at<double>(ws, L.sI);
   launch_adjoint(p, s);
-  launch_adjoint_reduce(p.lineT, p.lineTv, p.lineP, cnt + CNT_KEPT, tr->n, dL_dT, dL_dTvib, dL_dP, s);
+  // the Q partial sums are final by now: their buffer holds the reduction's per-CTA totals
+  if (adjoint_reduce_scratch_bytes() > (size_t)kQBlocks * kQMoments * 8)
+    return fail(PXC_ERR_CAPACITY, "backward: reduction scratch larger than the Q partial buffer");
+  launch_adjoint_reduce(p.lineT, p.lineTv, p.lineP, cnt + CNT_KEPT, at<double>(ws, L.qpart), dL_dT, dL_dTvib, dL_dP, s);
   x->last_nseg = 0;  // the adjoint does not bin lines into segments
   ws->last_nc = 1;
   return cuda_check("cross_section_backward");

@@ -67,12 +67,14 @@ struct CondDev {
   int32_t kind;
 };
 
-// Compact per-state record read by the intensity pass for its rejection bound:
-// E exact, g, and log2 of the Boltzmann factor in FP32.
-struct __align__(16) StateFast {
+// Per-state record of the intensity pass, one 32-byte sector: E exact, the FP64 Boltzmann factor,
+// g, and log2 of the Boltzmann factor in FP32 (for the rejection bound).
+struct __align__(32) StateFast {
   double E;
+  double b;
   int32_t g;
   float lb;
+  int64_t pad;
 };
 
 // Work item of the profile kernel: lines [begin, end) of the sorted list onto
