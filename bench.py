@@ -303,6 +303,9 @@ def main_pxc(args):
         return tr, prof
 
     wgt = torch.from_numpy(w.weights()).to(dev) if args.backward else None
+    if args.backward:
+        # the adjoint reads back the forward's kept, sorted line list (same arrays in between)
+        ws.set_reuse_forward(True)
 
     def step(count=None):
         if args.backward:
@@ -471,11 +474,11 @@ def main_pxc(args):
                               "note": "warp-instruction issue slots of the algorithmic work (one per SMSP per clock)"},
                     "launch_ms": prof_launch_ms, "launches_per_step": prof_n / max(args.steps, 1)}
     # algorithmic bytes of one intensity launch: the line arrays read once (upper, lower, A),
-    # (key, index, FP64 I) written per kept line, and the state-code table (12-bit codes, 3 bytes
-    # per 2 states) read once
+    # (key, index, FP64 I) written per kept line, and the state-code table (12-bit codes, five per
+    # 64-bit word) read once
     kept_per_launch = kept / nchunks
     a_bytes = 4 if w.A_f32 else 8
-    per_launch_bytes = chunk * (4 + 4 + a_bytes) + kept_per_launch * (8 + 4 + 8) + (w.n_states + 1) // 2 * 3
+    per_launch_bytes = chunk * (4 + 4 + a_bytes) + kept_per_launch * (8 + 4 + 8) + (w.n_states + 4) // 5 * 8
     int_launch_ms = int_ms / max(int_n, 1)
     ach_hbm = per_launch_bytes / (int_launch_ms / 1e3) / 1e9 if int_n else 0.0
     roof_int = {"bound": "hbm", "achieved": ach_hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -622,19 +625,22 @@ def run_extras(args, pxc, torch, dev, synth):
     wt = torch.from_numpy(w.weights()).to(dev)
     wsf = pxc.Workspace(max_states=w.n_states, max_lines=w.n_trans, max_grid=w.n_grid, device=dev)
     ms_f = timed(lambda: pxc.pxc_cross_section(wsf, st, tr, cond, grid, prof), reps=3)
+    wsf.set_reuse_forward(True)  # the adjoint reads back the forward's kept, sorted line list
 
     def fb():
         pxc.pxc_cross_section(wsf, st, tr, cond, grid, prof)
         pxc.pxc_cross_section_backward(wsf, st, tr, cond, grid, prof, wt)
 
     ms_fb = timed(fb, reps=3)
+    wsf.set_reuse_forward(False)
     ev_f = wsf.stats()["evals_nonzero"]
     ms_bwd = max(ms_fb - ms_f, 1e-6)
     res["fwd_bwd"] = {"workload": w.name, "lines": w.n_trans, "fwd_ms": ms_f, "fwd_bwd_ms": ms_fb,
                       "ratio": ms_fb / ms_f, "evals": ev_f, "fwd_evals_per_s": ev_f / (ms_f / 1e3),
                       "bwd_evals_per_s": ev_f / (ms_bwd / 1e3),
-                      "note": "backward = adjoint pass (intensity, sort and one k_adjoint launch); its evaluations "
-                              "are the forward's, each with the W4 value and its z-derivative"}
+                      "note": "backward = one k_adjoint launch over the forward's kept, sorted lines "
+                              "(pxc_set_reuse_forward) and the fixed-order reduction; its evaluations are the "
+                              "forward's, each with the W4 value and its z-derivative"}
 
     # vibronic-density populations on the same list (T_rot = 1200 K), absorption and emission
     nv = torch.from_numpy(w.vib_densities()).to(dev)

@@ -272,6 +272,17 @@ pxc_status pxc_cross_section_backward(pxc_workspace* ws, const pxc_states* state
                                       double* dL_dP, float* dL_dgamma_ref, float* dL_dA,
                                       cudaStream_t stream);
 
+/* Reuse of the forward's line list by the adjoint (off by default).  When on, a single-condition
+ * pxc_cross_section on a wavenumber grid (absorption, not in accumulate mode, a kind with an
+ * adjoint) also keeps the sorted per-line ids and A the adjoint needs, and a following
+ * pxc_cross_section_backward whose arguments (arrays, sizes, condition, grid, profile, threshold)
+ * are identical to that call's skips the intensity pass, sort and preparation and reads the
+ * forward's kept, sorted lines instead.  Any other call on the workspace in between (or this
+ * call) discards the kept list.  The caller guarantees that the contents of the arrays have not
+ * changed since the forward call (as an autograd forward/backward pair does); the backward's
+ * results are then bit-identical to those without reuse. */
+pxc_status pxc_set_reuse_forward(pxc_workspace* ws, int32_t on);
+
 /* Diagnostics of the last pxc_cross_section / backward call on this workspace
  * (host values; synchronises the stream).  Counts are over the last condition. */
 typedef struct {

@@ -82,7 +82,7 @@ ABI_FUNCTIONS = [
     "pxc_cross_section_streamed", "pxc_kernel_launches", "pxc_set_timing", "pxc_get_timing",
     "pxc_partition_function_noalloc", "pxc_set_tile", "pxc_get_tile", "pxc_autotune",
     "pxc_set_emission", "pxc_cooling_function", "pxc_set_wait_limit", "pxc_pipe_rates_buffer_bytes",
-    "pxc_pipe_rates", "pxc_set_graphs", "pxc_graph_stats",
+    "pxc_pipe_rates", "pxc_set_graphs", "pxc_graph_stats", "pxc_set_reuse_forward",
 ]
 
 # Profile-kernel tile configurations (segment width in grid points), as compiled into the library.
@@ -125,6 +125,7 @@ def load(path: str | None = None):
     L.pxc_set_emission.argtypes = [c_ptr, ctypes.c_int]
     L.pxc_set_wait_limit.argtypes = [c_ptr, c_i64]
     L.pxc_set_graphs.argtypes = [c_ptr, ctypes.c_int]
+    L.pxc_set_reuse_forward.argtypes = [c_ptr, ctypes.c_int32]
     L.pxc_graph_stats.argtypes = [c_ptr, P(c_i64), P(c_i64), P(c_i32)]
     L.pxc_cooling_function.argtypes = [c_ptr, P(pxc_states), P(pxc_transitions), P(pxc_condition), c_i32,
                                        c_ptr, c_ptr, c_ptr]
@@ -303,6 +304,11 @@ class Workspace:
         """Capture distinct pxc_cross_section calls into CUDA graphs and replay identical ones."""
         _check(load().pxc_set_graphs(self.h, int(on)))
 
+    def set_reuse_forward(self, on: bool):
+        """Let pxc_cross_section_backward reuse the line list of an identical preceding forward call
+        (the caller guarantees the arrays are unchanged in between)."""
+        _check(load().pxc_set_reuse_forward(self.h, int(on)))
+
     def graph_stats(self) -> dict:
         cap, rep, cached = c_i64(0), c_i64(0), c_i32(0)
         _check(load().pxc_graph_stats(self.h, ctypes.byref(cap), ctypes.byref(rep), ctypes.byref(cached)))
@@ -480,6 +486,8 @@ class CrossSection(torch.autograd.Function):
         prof = Profile(profile.kind, profile.cutoff, profile.mass_da, profile.hwhm, gamma_ref.detach(),
                        profile.n_T, profile.T_ref)
         tr = Transitions(upper, lower, A.detach())
+        # the backward pass reads back this call's kept, sorted line list (same arrays by construction)
+        ws.set_reuse_forward(True)
         sig, e = pxc_cross_section(ws, states, tr, cond, grid, prof, threshold)
         ctx.save_for_backward(T, T_vib, P, gamma_ref, A)
         ctx.ws, ctx.states, ctx.upper, ctx.lower, ctx.grid, ctx.profile, ctx.threshold = \

@@ -30,6 +30,7 @@ struct GridP {
   int exact_bounds;               // 0: evaluate the window per line
   double wl_unit;                 // 0: wavenumber grid; U > 0: wavelength grid with nu = U / lambda
   double nu_span_lo, nu_span_hi;  // every kept line has nu in [lo, hi] (the state-code prefilter)
+  double inv_dnu;                 // 1 / dnu rounded to FP64 (a first guess of the window quotients)
 };
 
 struct SlotP {                    // one temperature pair
@@ -48,15 +49,16 @@ void launch_boltzmann(const pxc_states* st, const SlotP* slots_dev, int nslot, d
 // Per-state 12-bit energy codes for the intensity pass's prefilter: q = floor((E - Emin) inv_res)
 // for finite E (q <= kCodeMax), kCodeNone otherwise.  For every finite E, Emin + (q - 1) / inv_res
 // <= E <= Emin + (q + 2) / inv_res, so nu = E_u - E_l lies within (q_u - q_l -+ 3) / inv_res.
-// Two states share three bytes (state 2p: byte 3p and the low half of byte 3p + 1; state 2p + 1: the
-// high half of byte 3p + 1 and byte 3p + 2): 75 MB for 5e7 states, which the random gathers of the
-// pass find in L2 far more often than the 100 MB of 16-bit codes (measured 0.9 against 1.45 ms
-// per 1e8 lines of gathers), for ~5 % candidates instead of ~3 %.  (8-bit codes, small enough
-// for one die's L2 half, send ~14 % of the lines to the full test.)
-using code_t = uint8_t;
+// Five codes share one 64-bit word (state 5w + i at bits 12i .. 12i + 11; 80 MB for 5e7 states), so
+// one 8-byte load fetches a code: the pass is limited by the L1 sectors of its random gathers, and
+// a layout with codes across byte boundaries (three bytes per two states, 75 MB) needed two loads
+// per code.  The random gathers find the table in L2 far more often than the 100 MB of 16-bit
+// codes (measured 0.9 against 1.45 ms per 1e8 lines of gathers), for ~6 % candidates instead of
+// ~3 %.  (8-bit codes, small enough for one die's L2 half, send ~40 % of the lines to the full test.)
+using code_t = uint64_t;
 constexpr int kCodeNone = 4095;
 constexpr int kCodeMax = kCodeNone - 1;
-inline size_t code_bytes(int64_t n_states) { return (size_t)((n_states + 1) / 2) * 3; }
+inline size_t code_bytes(int64_t n_states) { return (size_t)((n_states + 4) / 5) * 8; }
 struct QuantHdr {
   double Emin, inv_res;
   float res_f;      // 1 / inv_res rounded up
@@ -158,8 +160,10 @@ void launch_compact_nonzero(const int4* pos, const float2* par, const float* Is,
                             int64_t n_max, uint32_t* bcount, unsigned long long* nnz_dev, int4* pos_c, float2* par_c,
                             float* Is_c, cudaStream_t s);
 
+// Adds each (condition, segment) group's partial rows to its sigma row (cond_list as in launch_items).
 void launch_reduce_partials(const Item* items, const int32_t* seg_items, int64_t nseg, int seg, int n_c,
-                            const float* partial, float* sigma, int64_t n_grid, cudaStream_t s);
+                            const float* partial, float* sigma, int64_t n_grid, const int32_t* cond_list,
+                            cudaStream_t s);
 
 void launch_stick_out(const double* Iv, const uint64_t* key, int64_t n, const int32_t* kexp, float* I_scaled,
                       cudaStream_t s);

@@ -21,6 +21,22 @@ __device__ __forceinline__ void set_err(unsigned* err, unsigned bits) { atomicOr
 // |nu_i - nu| <= cut are those with U/(nu + cut) <= lambda_i <= U/(nu - cut):
 // ceil((U/(nu + cut) - lambda_min)/dlambda) .. floor((U/(nu - cut) - lambda_min)/dlambda), the
 // last point when nu <= cut.
+// ceil(num / den) and floor(num / den) of the IEEE quotient without a division in almost every
+// case: q = num * inv (inv = 1/den rounded) is within 2^-52 |q| of num / den, so when q is farther
+// than 2^-51 |q| from the nearest integer the quotient has the same ceiling and floor; otherwise
+// (an exact or near-integer quotient, num = 0) the rounded division decides.
+__device__ __forceinline__ bool quotient_clear(double q) {
+  return fabs(q - rint(q)) > 0x1p-51 * fabs(q);
+}
+__device__ __forceinline__ double ceil_div(double num, double den, double inv) {
+  const double q = num * inv;
+  return quotient_clear(q) ? ceil(q) : ceil(__ddiv_rn(num, den));
+}
+__device__ __forceinline__ double floor_div(double num, double den, double inv) {
+  const double q = num * inv;
+  return quotient_clear(q) ? floor(q) : floor(__ddiv_rn(num, den));
+}
+
 __device__ __forceinline__ bool exact_window(double nu, const GridP& gp, int64_t* lo, int64_t* hi) {
   double a, b;
   if (gp.wl_unit > 0.0) {
@@ -29,8 +45,8 @@ __device__ __forceinline__ bool exact_window(double nu, const GridP& gp, int64_t
             ? floor(__ddiv_rn(__dsub_rn(__ddiv_rn(gp.wl_unit, __dsub_rn(nu, gp.cut)), gp.nu_min), gp.dnu))
             : (double)(gp.n - 1);
   } else {
-    a = ceil(__ddiv_rn(__dsub_rn(__dsub_rn(nu, gp.cut), gp.nu_min), gp.dnu));
-    b = floor(__ddiv_rn(__dsub_rn(__dadd_rn(nu, gp.cut), gp.nu_min), gp.dnu));
+    a = ceil_div(__dsub_rn(__dsub_rn(nu, gp.cut), gp.nu_min), gp.dnu, gp.inv_dnu);
+    b = floor_div(__dsub_rn(__dadd_rn(nu, gp.cut), gp.nu_min), gp.dnu, gp.inv_dnu);
   }
   double top = (double)(gp.n - 1);
   if (!(b >= 0.0) || a > top || a > b) return false;
@@ -48,6 +64,14 @@ __device__ __forceinline__ uint64_t line_key(double nu, const GridP& gp) {
 __device__ __forceinline__ double key_nu(uint64_t k, const GridP& gp) {
   return __longlong_as_double((long long)(gp.wl_unit > 0.0 ? ~k & 0x7fffffffffffffffull : k));
 }
+
+// v 2^-k, bit for bit as ldexp(v, -k): a multiplication by the exact power of two while 2^-k is a
+// normal double (both are the correctly rounded product), ldexp itself otherwise.
+__device__ __forceinline__ bool pow2_normal(int k) { return k >= -1000 && k <= 1022; }
+__device__ __forceinline__ double pow2_scale(int k) {
+  return pow2_normal(k) ? __longlong_as_double((long long)(1023 - k) << 52) : 0.0;
+}
+__device__ __forceinline__ double scale_by(double v, int k, double s) { return pow2_normal(k) ? v * s : ldexp(v, -k); }
 
 __device__ __forceinline__ bool window_meets_grid(double nu, const GridP& gp) {
   if (gp.exact_bounds) return nu >= gp.nu_keep_lo && nu <= gp.nu_keep_hi;
@@ -91,8 +115,10 @@ __device__ const double kExp2J64[64] = {
 __device__ __forceinline__ double exp_tang(double x, const double* __restrict__ tab) {
   const long long xb = __double_as_longlong(x);
   if ((xb & 0x7fffffffffffffffll) >= 0x4085e00000000000ll) return exp(x);  // |x| >= 700 or NaN
-  const double n = rint(x * 92.332482616893657);                           // 64 / ln2
-  const int ni = (int)n;
+  // n = x 64/ln2 rounded to the nearest integer: adding 1.5 2^52 leaves n in the low word
+  const double tn = fma(x, 92.332482616893657, 0x1.8p52);                  // 64 / ln2
+  const int ni = __double2loint(tn);
+  const double n = tn - 0x1.8p52;
   const double r = fma(-n, 0x1.abc9e3b39803fp-62, fma(-n, 0x1.62e42fefa39efp-7, x));  // ln2/64, two parts
   const double q = r * fma(fma(fma(fma(r, 1.0 / 120.0, 1.0 / 24.0), r, 1.0 / 6.0), r, 0.5), r, 1.0);
   const double t = tab[ni & 63];
@@ -123,7 +149,8 @@ __global__ void __launch_bounds__(kThreadsQ) k_boltzmann(const double* __restric
     unsigned bad = 0;
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
       double e = E[s];
-      double b = 0.0, lb = -INFINITY;
+      double b = 0.0;
+      float lb = -INFINITY;
       // NaN / infinity from the exponent bits (integer tests, off the FP64 pipe)
       const unsigned long long eb = (unsigned long long)__double_as_longlong(e);
       const bool nonfinite = (eb & 0x7ff0000000000000ull) == 0x7ff0000000000000ull;
@@ -152,8 +179,8 @@ __global__ void __launch_bounds__(kThreadsQ) k_boltzmann(const double* __restric
           bad |= ERRB_OVERFLOW;
         } else {
           b = w * exp_tang(x, tab);
-          lb = x * 1.4426950408889634;
-          if (dens) lb += log2(w);
+          // log2 b for the FP32 rejection bound (its margin absorbs the FP32 rounding here)
+          lb = dens ? (float)(x * 1.4426950408889634 + log2(w)) : (float)x * 1.44269504f;
           double term = (double)g[s] * b;
           q0 += term;
           q1 = fma(term, er, q1);                // times c2 / T^2 in k_qfinal: dQ/dT (or dQ/dT_rot)
@@ -166,9 +193,9 @@ __global__ void __launch_bounds__(kThreadsQ) k_boltzmann(const double* __restric
         StateFast r;
         r.E = e;
         r.b = b;
-        r.g = g[s];
-        r.lb = (float)lb;
-        r.pad = 0;
+        r.g = (double)g[s];
+        r.gf = (float)g[s];
+        r.lb = lb;
         sfast[s] = r;
       }
     }
@@ -329,13 +356,16 @@ __global__ void __launch_bounds__(256) k_state_quant(const double* __restrict__ 
                                                      code_t* __restrict__ code, QuantHdr* __restrict__ hdr) {
   const QuantHdr h = quant_header(words);
   if (blockIdx.x == 0 && threadIdx.x == 0) *hdr = h;
-  const int64_t np = (n + 1) / 2;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
-    const int q0 = quant_code(E[2 * p], h);
-    const int q1 = 2 * p + 1 < n ? quant_code(E[2 * p + 1], h) : kCodeNone;
-    code[3 * p] = (code_t)(q0 & 0xff);
-    code[3 * p + 1] = (code_t)((q0 >> 8) | ((q1 & 0xf) << 4));
-    code[3 * p + 2] = (code_t)(q1 >> 4);
+  const int64_t nw = (n + 4) / 5;
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x) {
+    code_t word = 0;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      const int64_t st = 5 * w + i;
+      const int q = st < n ? quant_code(E[st], h) : kCodeNone;
+      word |= (code_t)q << (12 * i);
+    }
+    code[w] = word;
   }
 }
 
@@ -468,20 +498,13 @@ __device__ __forceinline__ uint32_t block_rank(bool flag, uint32_t* wsum, uint32
   return before + __popc(m & ((1u << lane) - 1u));
 }
 
-// 12-bit code of state s (kept in L2 with the evict-last policy: the state codes are re-read at
-// random).  A pair of states shares 3 bytes: state 2k is byte 3k plus the low nibble of byte 3k+1,
-// state 2k+1 the high nibble of byte 3k+1 plus byte 3k+2; either way two consecutive bytes starting
-// at 3k + (s & 1), loaded without a branch so that every code load of a round is in flight at once.
-__device__ __forceinline__ int ld_byte(const code_t* p, uint64_t pol) {
-  unsigned short v;
-  asm("ld.global.nc.L2::cache_hint.u8 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(pol));
-  return (int)v;
-}
+// 12-bit code of state s: one 8-byte load of its word (kept in L2 with the evict-last policy: the
+// state codes are re-read at random), then the code's 12 bits.
 __device__ __forceinline__ int ld_code(const code_t* tab, int32_t s, uint64_t pol) {
-  const int odd = s & 1;
-  const code_t* p = tab + 3 * (int64_t)(s >> 1) + odd;
-  const int b0 = ld_byte(p, pol), b1 = ld_byte(p + 1, pol);
-  return odd ? (b0 >> 4) | (b1 << 4) : b0 | ((b1 & 0xf) << 8);
+  const unsigned su = (unsigned)s, w = su / 5u;
+  unsigned long long v;
+  asm("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(tab + w), "l"(pol));
+  return (int)(v >> (12u * (su - 5u * w))) & 0xfff;
 }
 
 // Per-block constants of the compacting intensity pass (computed once per CTA by one thread).
@@ -548,7 +571,8 @@ __device__ __forceinline__ bool line_test(const LineIn& x, int A32, int64_t ns, 
   const int32_t u = x.u, l = x.l;
   const bool finite = A32 ? (x.ab & 0x7f800000ull) != 0x7f800000ull
                           : (x.ab & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
-  if (u < 0 || u >= ns || l < 0 || l >= ns) {
+  // ids in [0, ns): one unsigned comparison each (state counts are below 2^31)
+  if ((unsigned)u >= (unsigned)ns || (unsigned)l >= (unsigned)ns) {
     *bad |= ERRB_ID;
     return false;
   }
@@ -682,6 +706,7 @@ __global__ void __launch_bounds__(kThreadsI) k_lines_exact(const int32_t* __rest
         }
         if (ok) {
           const double A = A32 ? (double)__uint_as_float((unsigned)ab) : __longlong_as_double((long long)ab);
+          const float Af = A32 ? __uint_as_float((unsigned)ab) : (float)A;
           const StateFast fu = sfast[u], fl = sfast[l];
           nu = __dsub_rn(fu.E, fl.E);
           if (gp.exact_bounds) {
@@ -697,18 +722,18 @@ __global__ void __launch_bounds__(kThreadsI) k_lines_exact(const int32_t* __rest
               const float nuf = (float)nu;
               float P, lbb;
               if (bp.mode == IMODE_EMISSION) {
-                P = (float)fu.g * (float)A * nuf * (float)kTwoHC2;
+                P = fu.gf * Af * nuf * (float)kTwoHC2;
                 lbb = fu.lb;
               } else {
                 const float m = bp.lte ? fminf(1.f, bp.c2_T * nuf) : 1.f;
-                P = (float)fu.g * (float)A * m / (nuf * nuf);
+                P = fu.gf * Af * m / (nuf * nuf);
                 lbb = fmaxf(fu.lb, fl.lb);
               }
               if (__log2f(P) + lbb + c.l2invQ < bp.log2_thr) keep = false;
             }
             if (keep) {
               double num, den;
-              line_value(bp.mode, bp.c2_Td, (double)fu.g, A, c.invQ, fl.b, fu.b, nu, &num, &den);
+              line_value(bp.mode, bp.c2_Td, fu.g, A, c.invQ, fl.b, fu.b, nu, &num, &den);
               keep = fabs(num) >= threshold * den;
               if (keep) I = num / den;
             }
@@ -783,23 +808,60 @@ void launch_compact_staged(const uint64_t* kstage, const uint32_t* istage, const
 }
 
 // ------------------------------------------------------------------ exclusive scan of block counts (one CTA)
-__global__ void k_scan_counts(uint32_t* __restrict__ c, int64_t n, unsigned long long* total) {
-  __shared__ unsigned long long part[1024];
-  int64_t per = (n + blockDim.x - 1) / blockDim.x;
-  int64_t a = threadIdx.x * per, b = a + per < n ? a + per : n;
-  unsigned long long s = 0;
-  for (int64_t i = a; i < b; ++i) s += c[i];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long run = 0;
-    for (int i = 0; i < (int)blockDim.x; ++i) { unsigned long long v = part[i]; part[i] = run; run += v; }
-    *total = run;
-    c[n] = (uint32_t)run;
+// In-place exclusive scan of n counts (16-byte aligned) by one CTA of 1024 threads, total at [n] and in *total:
+// tiles of 4096 counts, each thread four consecutive ones (one 16-byte load and store), a warp
+// scan and a scan of the 32 warp totals, the running carry between tiles.
+__global__ void __launch_bounds__(1024) k_scan_counts(uint32_t* __restrict__ c, int64_t n,
+                                                      unsigned long long* total) {
+  __shared__ unsigned long long wsum[32];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  unsigned long long carry = 0;
+  for (int64_t base = 0; base < n; base += 4096) {
+    const int64_t i0 = base + 4 * (int64_t)t;
+    uint32_t v0 = 0, v1 = 0, v2 = 0, v3 = 0;
+    if (i0 + 3 < n) {
+      const uint4 q = *reinterpret_cast<const uint4*>(c + i0);
+      v0 = q.x; v1 = q.y; v2 = q.z; v3 = q.w;
+    } else {
+      if (i0 < n) v0 = c[i0];
+      if (i0 + 1 < n) v1 = c[i0 + 1];
+      if (i0 + 2 < n) v2 = c[i0 + 2];
+    }
+    const unsigned long long sum = (unsigned long long)v0 + v1 + v2 + v3;
+    unsigned long long x = sum;  // inclusive scan over the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      unsigned long long y = wsum[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long z = __shfl_up_sync(0xffffffffu, y, o);
+        if (lane >= o) y += z;
+      }
+      wsum[lane] = y;
+    }
+    __syncthreads();
+    const unsigned long long e0 = carry + (w ? wsum[w - 1] : 0ull) + x - sum;
+    const unsigned long long e1 = e0 + v0, e2 = e1 + v1, e3 = e2 + v2;
+    if (i0 + 3 < n) {
+      *reinterpret_cast<uint4*>(c + i0) = make_uint4((uint32_t)e0, (uint32_t)e1, (uint32_t)e2, (uint32_t)e3);
+    } else {
+      if (i0 < n) c[i0] = (uint32_t)e0;
+      if (i0 + 1 < n) c[i0 + 1] = (uint32_t)e1;
+      if (i0 + 2 < n) c[i0 + 2] = (uint32_t)e2;
+    }
+    carry += wsum[31];
+    __syncthreads();  // wsum is rewritten by the next tile
   }
-  __syncthreads();
-  unsigned long long run = part[threadIdx.x];
-  for (int64_t i = a; i < b; ++i) { uint32_t v = c[i]; c[i] = (uint32_t)run; run += v; }
+  if (t == 0) {
+    *total = carry;
+    c[n] = (uint32_t)carry;
+  }
 }
 
 void launch_scan_counts(uint32_t* bcount, int64_t nblk, unsigned long long* total, cudaStream_t s) {
@@ -1041,6 +1103,7 @@ __global__ void __launch_bounds__(256) k_prepare(const uint64_t* __restrict__ sk
                                                  unsigned long long* __restrict__ counters) {
   const int64_t n = (int64_t)*n_dev;
   const int k = Iv ? kexp[0] : 0;
+  const double sk = pow2_scale(k);
   unsigned long long ev = 0, evnz = 0, nz = 0;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
     double nu = key_nu(skey[j], gp);
@@ -1057,7 +1120,7 @@ __global__ void __launch_bounds__(256) k_prepare(const uint64_t* __restrict__ sk
     unsigned long long wsz = (unsigned long long)(b - a + 1);
     ev += wsz;
     if (Iv) {
-      float is = (float)ldexp(Iv[t], -k);
+      float is = (float)scale_by(Iv[t], k, sk);
       Is[j] = is;
       if (is != 0.f) { evnz += wsz; ++nz; }
     }
@@ -1139,8 +1202,9 @@ __global__ void k_scale(const double* __restrict__ sI, const unsigned long long*
                         const int32_t* __restrict__ kexp, float* __restrict__ Is) {
   const int64_t n = (int64_t)*n_dev;
   const int k = kexp[0];
+  const double sk = pow2_scale(k);
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
-    Is[j] = (float)ldexp(sI[j], -k);
+    Is[j] = (float)scale_by(sI[j], k, sk);
 }
 
 void launch_scale(const double* sI, const unsigned long long* n_dev, int64_t n_max, const int32_t* kexp,
@@ -1281,11 +1345,11 @@ void launch_items(const int32_t* segr, int64_t nseg, int n_c, int item_lines, in
 // Adds the partial rows of split segments to sigma, in item order (deterministic).
 __global__ void k_reduce_partials(const Item* __restrict__ items, const int32_t* __restrict__ seg_items, int64_t nseg,
                                   int seg, const float* __restrict__ partial, float* __restrict__ sigma,
-                                  int64_t n_grid) {
+                                  int64_t n_grid, const int32_t* __restrict__ cond_list) {
   int64_t gi = blockIdx.x;
   int32_t f = seg_items[gi], e = seg_items[gi + 1];
   if (e - f <= 1) return;
-  int64_t s = gi % nseg, c = gi / nseg;
+  const int64_t s = gi % nseg, c = cond_list ? cond_list[gi / nseg] : gi / nseg;
   for (int p = threadIdx.x; p < seg; p += blockDim.x) {
     int64_t i = s * seg + p;
     if (i >= n_grid) break;
@@ -1296,8 +1360,10 @@ __global__ void k_reduce_partials(const Item* __restrict__ items, const int32_t*
 }
 
 void launch_reduce_partials(const Item* items, const int32_t* seg_items, int64_t nseg, int seg, int n_c,
-                            const float* partial, float* sigma, int64_t n_grid, cudaStream_t s) {
-  k_reduce_partials<<<(unsigned)(nseg * n_c), 128, 0, s>>>(items, seg_items, nseg, seg, partial, sigma, n_grid);
+                            const float* partial, float* sigma, int64_t n_grid, const int32_t* cond_list,
+                            cudaStream_t s) {
+  k_reduce_partials<<<(unsigned)(nseg * n_c), 128, 0, s>>>(items, seg_items, nseg, seg, partial, sigma, n_grid,
+                                                           cond_list);
   note_launches(1);
 }
 
@@ -1305,8 +1371,9 @@ void launch_reduce_partials(const Item* items, const int32_t* seg_items, int64_t
 __global__ void k_stick_out(const double* __restrict__ Iv, const uint64_t* __restrict__ key, int64_t n,
                             const int32_t* __restrict__ kexp, float* __restrict__ out) {
   const int k = kexp[0];
+  const double sk = pow2_scale(k);
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
-    out[t] = key[t] == kSentinelKey ? 0.f : (float)ldexp(Iv[t], -k);
+    out[t] = key[t] == kSentinelKey ? 0.f : (float)scale_by(Iv[t], k, sk);
 }
 
 void launch_stick_out(const double* Iv, const uint64_t* key, int64_t n, const int32_t* kexp, float* I_scaled,

@@ -799,20 +799,28 @@ __device__ __forceinline__ void eval_slow(const LineC& c, int wbase, int lane, c
 // fast lines from the front, the others from the back.  The last warp to finish reading a
 // stage buffer re-arms it with the copy kNB stages ahead, so warps drift apart by up to
 // kNB - 1 stages instead of waiting for each other at every stage.
+// Stage buffers per CTA: three for multi-warp CTAs (warps drift by up to two stages); two for
+// one-warp CTAs, whose single warp never waits for another (the smaller shared-memory footprint
+// lets more of them reside on an SM).
 #ifndef PXC_STAGE_BUFFERS
 #define PXC_STAGE_BUFFERS 3
 #endif
-constexpr int kNB = PXC_STAGE_BUFFERS;
+#ifndef PXC_STAGE_BUFFERS_1W
+#define PXC_STAGE_BUFFERS_1W 2
+#endif
+template <int THREADS>
+constexpr int stage_buffers() { return THREADS == 32 ? PXC_STAGE_BUFFERS_1W : PXC_STAGE_BUFFERS; }
 
 template <int THREADS, int SL>
 constexpr size_t profile_smem() {
-  return (size_t)kNB * SL * (16 + 8 + 4) + (size_t)(THREADS / 32) * SL * sizeof(LineC);
+  return (size_t)stage_buffers<THREADS>() * SL * (16 + 8 + 4) + (size_t)(THREADS / 32) * SL * sizeof(LineC);
 }
 
 template <int KIND, int THREADS, int PTS, int SL, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB) k_profile(const ProfP p) {
   constexpr int SEG = THREADS * PTS, WPTS = 32 * PTS, NW = THREADS / 32;
   constexpr int SBYTES = SL * (16 + 8 + 4);
+  constexpr int kNB = stage_buffers<THREADS>();
   extern __shared__ __align__(128) unsigned char dyn_smem[];
   unsigned char* raw = dyn_smem;                                              // [kNB][SBYTES]
   LineC* wl = reinterpret_cast<LineC*>(dyn_smem + kNB * SBYTES);             // [NW][SL]
@@ -972,7 +980,15 @@ __global__ void __launch_bounds__(THREADS, MINB) k_profile(const ProfP p) {
 // Segment widths 128, 256, 1024 and 2048 points.  (One-warp tiles of 256 and 512 points, with
 // fewer line-warp constant builds per evaluation, measured slower than tile 0 on the 1e9-line
 // list: 12.4 and 17.9 against 11.4 ms per 1e8-line call.)
-#define PXC_TILES(X) X(0, 32, 4, 64, 32) X(1, 64, 4, 64, 16) X(2, 128, 8, 64, 6) X(3, 128, 16, 128, 4)
+#ifndef PXC_TILE0_SL
+#define PXC_TILE0_SL 64
+#endif
+#ifndef PXC_TILE0_PTS
+#define PXC_TILE0_PTS 4
+#define PXC_TILE0_MINB 32
+#endif
+#define PXC_TILES(X) \
+  X(0, 32, PXC_TILE0_PTS, PXC_TILE0_SL, PXC_TILE0_MINB) X(1, 64, 4, 64, 16) X(2, 128, 8, 64, 6) X(3, 128, 16, 128, 4)
 
 int tile_seg(int tile) {
 #define X(i, T, P, S, M) if (tile == i) return T * P;

@@ -59,7 +59,9 @@ Layout make_layout(const pxc_capacity& c) {
   L.partial_floats = 0;
   for (int t = 0; t < kNumTiles; ++t)
     L.partial_floats = std::max<int64_t>(L.partial_floats, split_rows(ml, tile_seg(t)) * tile_seg(t));
-  L.max_items = std::max<int64_t>(L.max_seg + L.partial_floats / kSegMin, L.max_cond * L.max_seg);
+  // one item per (condition, segment) plus the split items, whose partial rows the partial-row
+  // buffer bounds (batched calls split too)
+  L.max_items = L.max_cond * L.max_seg + L.partial_floats / kSegMin;
   L.is_stride = ((ml + kPad) + 3) & ~(int64_t)3;
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t r = o; o += al(bytes); return r; };
@@ -156,6 +158,7 @@ double bitsd(uint64_t b) { double d; memcpy(&d, &b, 8); return d; }
 GridP make_gridp(const pxc_grid& g, double cut) {
   GridP gp{};
   gp.nu_min = g.nu_min; gp.dnu = g.dnu; gp.cut = cut; gp.n = g.n;
+  gp.inv_dnu = 1.0 / g.dnu;
   gp.wl_unit = g.wl_unit;
   gp.exact_bounds = 0;
   const double last = g.nu_min + (double)(g.n - 1) * g.dnu;
@@ -235,6 +238,10 @@ struct WsExtra {
   cudaStream_t cap_stream;
   std::vector<GraphEntry> gcache;  // most recently used last
   int64_t graph_hits, graph_captures;
+  // pxc_set_reuse_forward: the arguments of the single-condition call whose kept, sorted line list
+  // (with the per-line ids and A the adjoint needs) the workspace holds; empty when none
+  int reuse_fwd;
+  std::vector<unsigned char> fwd_key;
 };
 
 // Records a timing event for `pass` (start or end) when timing is on.
@@ -489,12 +496,14 @@ pxc_status pxc_set_wait_limit(pxc_workspace* ws, int64_t cycles) {
 
 pxc_status pxc_set_emission(pxc_workspace* ws, int on) {
   if (!ws) return fail(PXC_ERR_ARG, "set_emission: null workspace");
+  X(ws)->fwd_key.clear();  // the workspace no longer holds a reusable line list
   X(ws)->emission = on ? 1 : 0;
   return PXC_OK;
 }
 
 pxc_status pxc_set_accumulate(pxc_workspace* ws, int on) {
   if (!ws) return fail(PXC_ERR_ARG, "null workspace");
+  X(ws)->fwd_key.clear();  // the workspace no longer holds a reusable line list
   ws->accumulate = on ? 1 : 0;
   if (!on) ws->cache_valid = 0;
   return PXC_OK;
@@ -522,6 +531,7 @@ pxc_status pxc_sync_status(pxc_workspace* ws, cudaStream_t s) {
 pxc_status pxc_partition_function(pxc_workspace* ws, const pxc_states* st, const pxc_condition* c, int32_t n_c,
                                   double* Q_out, double* dQ_out, cudaStream_t s) {
   if (!ws || !c || n_c < 1 || !Q_out) return fail(PXC_ERR_ARG, "partition_function: bad arguments");
+  X(ws)->fwd_key.clear();  // the workspace no longer holds a reusable line list
   pxc_status r = check_states(st);
   if (r) return r;
   WsExtra* x = X(ws);
@@ -546,6 +556,7 @@ pxc_status pxc_partition_function(pxc_workspace* ws, const pxc_states* st, const
 pxc_status pxc_cooling_function(pxc_workspace* ws, const pxc_states* st, const pxc_transitions* tr,
                                 const pxc_condition* c, int32_t n_c, double* W_out, double* Q_out, cudaStream_t s) {
   if (!ws || !c || n_c < 1 || !W_out) return fail(PXC_ERR_ARG, "cooling_function: bad arguments");
+  X(ws)->fwd_key.clear();  // the workspace no longer holds a reusable line list
   pxc_status r;
   if ((r = check_states(st)) || (r = check_trans(tr))) return r;
   WsExtra* x = X(ws);
@@ -576,6 +587,7 @@ pxc_status pxc_line_intensities(pxc_workspace* ws, const pxc_states* st, const p
                                 double* nu_out, float* I_scaled_out, int32_t* I_exp_out, int64_t* n_kept_out,
                                 cudaStream_t s) {
   if (!ws || !c || !I_exp_out) return fail(PXC_ERR_ARG, "line_intensities: bad arguments");
+  X(ws)->fwd_key.clear();  // the workspace no longer holds a reusable line list
   pxc_status r;
   if ((r = check_states(st)) || (r = check_trans(tr)) || (r = check_cond(*c, false, st))) return r;
   if (grid && (r = check_grid(grid, cutoff))) return r;
@@ -607,6 +619,37 @@ pxc_status pxc_line_intensities(pxc_workspace* ws, const pxc_states* st, const p
 }  // extern "C"
 
 namespace {
+
+template <typename T>
+void put(std::vector<unsigned char>& k, const T& v) {
+  const unsigned char* p = reinterpret_cast<const unsigned char*>(&v);
+  k.insert(k.end(), p, p + sizeof(T));
+}
+
+// Arguments that determine a single-condition call's kept, sorted line list (what the adjoint reads
+// back), and the workspace modes that change it.
+std::vector<unsigned char> list_key(pxc_workspace* ws, const pxc_states* st, const pxc_transitions* tr,
+                                    const pxc_condition& c, const pxc_grid* grid, const pxc_profile_args* pa,
+                                    double threshold) {
+  WsExtra* x = X(ws);
+  std::vector<unsigned char> k;
+  k.reserve(256);
+  put(k, st->E); put(k, st->g); put(k, st->E_vib); put(k, st->n); put(k, st->n_vib);
+  put(k, tr->upper); put(k, tr->lower); put(k, tr->A); put(k, tr->A_is_f32); put(k, tr->n);
+  put(k, c.T); put(k, c.T_vib); put(k, c.P);
+  put(k, grid->nu_min); put(k, grid->dnu); put(k, grid->n); put(k, grid->wl_unit);
+  put(k, pa->kind); put(k, pa->cutoff); put(k, pa->mass_da); put(k, pa->hwhm); put(k, pa->gamma_ref);
+  put(k, pa->n_T); put(k, pa->T_ref);
+  put(k, threshold); put(k, x->emission); put(k, ws->accumulate);
+  return k;
+}
+
+// Whether a call leaves a line list the adjoint may reuse (single condition, wavenumber grid, a
+// kind with an adjoint, no chunk accumulation).
+bool reusable_call(pxc_workspace* ws, int32_t n_c, const pxc_grid* grid, const pxc_profile_args* pa) {
+  return X(ws)->reuse_fwd && n_c == 1 && grid->wl_unit == 0.0 && pa->kind <= PXC_VOIGT && !ws->accumulate &&
+         !X(ws)->emission;
+}
 
 // Profile-kernel arguments over the sorted list of the call (all temperature slots' intensities).
 ProfP profile_params(pxc_workspace* ws, const pxc_profile_args* pa, const pxc_grid* grid, const CondDev* dcond,
@@ -693,7 +736,9 @@ pxc_status cross_section_direct(pxc_workspace* ws, const pxc_states* st, const p
   uint32_t* idxs[2] = {at<uint32_t>(ws, L.sidx0), at<uint32_t>(ws, L.sidx1)};
   int32_t* kexp = at<int32_t>(ws, L.kexp);
   if (n_c == 1) {
-    if ((r = front_plain(ws, st, tr, c[0], gp, pa, threshold, sigma_exp_out, sigma_out, grid->n, false, s))) return r;
+    // with pxc_set_reuse_forward, the sorted ids and A are gathered too, for a later adjoint
+    const bool gather = reusable_call(ws, n_c, grid, pa);
+    if ((r = front_plain(ws, st, tr, c[0], gp, pa, threshold, sigma_exp_out, sigma_out, grid->n, gather, s))) return r;
   } else {
     // geometry only: kept set from nu and the window; intensities per temperature slot in sorted order.
     // The geometry pass reads E through the state table, so fill it (first slot) first.
@@ -738,9 +783,11 @@ pxc_status cross_section_direct(pxc_workspace* ws, const pxc_states* st, const p
                              at<uint32_t>(ws, L.bcount), cnt + CNT_SLOT_NZ, at<int4>(ws, L.pos_c),
                              at<float2>(ws, L.par_c), at<float>(ws, L.Is_c), s);
       launch_segments(at<int4>(ws, L.pos_c), cnt + CNT_SLOT_NZ, nseg, seg, at<int32_t>(ws, L.segr), s);
-      launch_items(at<int32_t>(ws, L.segr), nseg, first[k + 1] - first[k], INT32_MAX / 2,
-                   at<int32_t>(ws, L.seg_items), at<Item>(ws, L.items), cnt, L.max_items, 0ll, max_partial,
-                   condlist + first[k], s);
+      // segments with many lines (lines piled up at one wavenumber) are split into items of
+      // similar size whose partial rows are added afterwards, as in single-condition calls
+      const int mk = first[k + 1] - first[k];
+      launch_items(at<int32_t>(ws, L.segr), nseg, mk, kItemLines, at<int32_t>(ws, L.seg_items),
+                   at<Item>(ws, L.items), cnt, L.max_items, 16ll * ctas_b, max_partial, condlist + first[k], s);
       ProfP p = profile_params(ws, pa, grid, dcond, sigma_out, x->wait_limit);
       p.pos = at<int4>(ws, L.pos_c);
       p.par = at<float2>(ws, L.par_c);
@@ -749,6 +796,8 @@ pxc_status cross_section_direct(pxc_workspace* ws, const pxc_states* st, const p
       tmark(ws, 2, true, s);
       launch_profile(p, tile, ctas_b, s);
       tmark(ws, 2, false, s);
+      launch_reduce_partials(at<Item>(ws, L.items), at<int32_t>(ws, L.seg_items), nseg, seg, mk,
+                             at<float>(ws, L.partial), sigma_out, grid->n, condlist + first[k], s);
     }
     for (int i = 0; i < n_c; ++i)
       cudaMemcpyAsync(sigma_exp_out + i, kexp + 2 * slot_of[i], 4, cudaMemcpyDeviceToDevice, s);
@@ -772,7 +821,7 @@ pxc_status cross_section_direct(pxc_workspace* ws, const pxc_states* st, const p
   tmark(ws, 2, false, s);
   if (n_c == 1)
     launch_reduce_partials(at<Item>(ws, L.items), at<int32_t>(ws, L.seg_items), nseg, seg, 1,
-                           at<float>(ws, L.partial), sigma_out, grid->n, s);
+                           at<float>(ws, L.partial), sigma_out, grid->n, nullptr, s);
   x->last_nseg = nseg;
   x->last_seg = seg;
   x->last_tile = tile;
@@ -780,11 +829,6 @@ pxc_status cross_section_direct(pxc_workspace* ws, const pxc_states* st, const p
   return cuda_check("cross_section");
 }
 
-template <typename T>
-void put(std::vector<unsigned char>& k, const T& v) {
-  const unsigned char* p = reinterpret_cast<const unsigned char*>(&v);
-  k.insert(k.end(), p, p + sizeof(T));
-}
 
 // Everything a captured call depends on besides the contents of device memory: the pointers and
 // sizes of every array, the conditions, grid, profile and threshold, and the workspace's modes.
@@ -804,7 +848,7 @@ std::vector<unsigned char> graph_key(pxc_workspace* ws, const pxc_states* st, co
   put(k, pa->n_T); put(k, pa->T_ref);
   put(k, threshold); put(k, sigma_out); put(k, sigma_exp_out);
   const int kind = pa->kind >= 0 && pa->kind < kNumKinds ? pa->kind : 0;
-  put(k, x->tile[kind][n_c > 1 ? 1 : 0]); put(k, x->emission); put(k, x->wait_limit);
+  put(k, x->tile[kind][n_c > 1 ? 1 : 0]); put(k, x->emission); put(k, x->wait_limit); put(k, x->reuse_fwd);
   (void)s;
   return k;
 }
@@ -844,11 +888,10 @@ pxc_status pxc_graph_stats(pxc_workspace* ws, int64_t* captures, int64_t* replay
   return PXC_OK;
 }
 
-pxc_status pxc_cross_section(pxc_workspace* ws, const pxc_states* st, const pxc_transitions* tr,
-                             const pxc_condition* c, int32_t n_c, const pxc_grid* grid, const pxc_profile_args* pa,
-                             double threshold, float* sigma_out, int32_t* sigma_exp_out, cudaStream_t s) {
-  if (!ws || !c || n_c < 1 || !sigma_out || !sigma_exp_out || !st || !tr || !grid || !pa)
-    return fail(PXC_ERR_ARG, "cross_section: bad arguments");
+static pxc_status cross_section_graphs(pxc_workspace* ws, const pxc_states* st, const pxc_transitions* tr,
+                                       const pxc_condition* c, int32_t n_c, const pxc_grid* grid,
+                                       const pxc_profile_args* pa, double threshold, float* sigma_out,
+                                       int32_t* sigma_exp_out, cudaStream_t s) {
   WsExtra* x = X(ws);
   if (!x->graphs || ws->accumulate || x->capturing)
     return cross_section_direct(ws, st, tr, c, n_c, grid, pa, threshold, sigma_out, sigma_exp_out, s);
@@ -907,6 +950,25 @@ pxc_status pxc_cross_section(pxc_workspace* ws, const pxc_states* st, const pxc_
   return launch_entry(ws, x->gcache.back(), s);
 }
 
+pxc_status pxc_cross_section(pxc_workspace* ws, const pxc_states* st, const pxc_transitions* tr,
+                             const pxc_condition* c, int32_t n_c, const pxc_grid* grid, const pxc_profile_args* pa,
+                             double threshold, float* sigma_out, int32_t* sigma_exp_out, cudaStream_t s) {
+  if (!ws || !c || n_c < 1 || !sigma_out || !sigma_exp_out || !st || !tr || !grid || !pa)
+    return fail(PXC_ERR_ARG, "cross_section: bad arguments");
+  WsExtra* x = X(ws);
+  x->fwd_key.clear();
+  const pxc_status r = cross_section_graphs(ws, st, tr, c, n_c, grid, pa, threshold, sigma_out, sigma_exp_out, s);
+  if (r == PXC_OK && reusable_call(ws, n_c, grid, pa)) x->fwd_key = list_key(ws, st, tr, c[0], grid, pa, threshold);
+  return r;
+}
+
+pxc_status pxc_set_reuse_forward(pxc_workspace* ws, int32_t on) {
+  if (!ws) return fail(PXC_ERR_ARG, "set_reuse_forward: null workspace");
+  X(ws)->reuse_fwd = on ? 1 : 0;
+  X(ws)->fwd_key.clear();
+  return PXC_OK;
+}
+
 pxc_status pxc_cross_section_backward(pxc_workspace* ws, const pxc_states* st, const pxc_transitions* tr,
                                       const pxc_condition* c, int32_t n_c, const pxc_grid* grid,
                                       const pxc_profile_args* pa, double threshold, const float* dL_dsigma,
@@ -929,8 +991,15 @@ pxc_status pxc_cross_section_backward(pxc_workspace* ws, const pxc_states* st, c
   if (grid->wl_unit != 0.0) return fail(PXC_ERR_ARG, "backward: wavenumber grids only");
   GridP gp = make_gridp(*grid, pa->cutoff);
   unsigned long long* cnt = at<unsigned long long>(ws, L.counters);
-  cudaMemsetAsync(cnt, 0, CNT_N * 8, s);
-  if ((r = front_plain(ws, st, tr, *c, gp, pa, threshold, nullptr, nullptr, grid->n, true, s))) return r;
+  // the line list of the preceding call, when pxc_set_reuse_forward is on and its arguments match
+  std::vector<unsigned char> key = list_key(ws, st, tr, *c, grid, pa, threshold);
+  const bool reuse = x->reuse_fwd && !x->fwd_key.empty() && x->fwd_key == key;
+  if (!reuse) {
+    x->fwd_key.clear();
+    cudaMemsetAsync(cnt, 0, CNT_N * 8, s);
+    if ((r = front_plain(ws, st, tr, *c, gp, pa, threshold, nullptr, nullptr, grid->n, true, s))) return r;
+    if (x->reuse_fwd) x->fwd_key = std::move(key);
+  }
   if (dL_dA) cudaMemsetAsync(dL_dA, 0, sizeof(float) * tr->n, s);
   if (dL_dgamma_ref) cudaMemsetAsync(dL_dgamma_ref, 0, sizeof(float) * tr->n, s);
   AdjP p{};
@@ -1013,6 +1082,7 @@ pxc_status pxc_autotune(pxc_workspace* ws, const pxc_states* st, const pxc_trans
                         double* ms_out, cudaStream_t s) {
   if (!ws || !pa || pa->kind < 0 || pa->kind >= kNumKinds || n_c < 1 || repeats < 1)
     return fail(PXC_ERR_ARG, "autotune: bad arguments");
+  X(ws)->fwd_key.clear();  // the workspace no longer holds a reusable line list
   if (ws->accumulate) return fail(PXC_ERR_ARG, "autotune: not in accumulate mode (runs the call repeatedly)");
   WsExtra* x = X(ws);
   const int b = n_c > 1 ? 1 : 0;
@@ -1130,6 +1200,7 @@ pxc_status pxc_cross_section_streamed(pxc_workspace* ws, const pxc_states* st, c
   if (!ws || !h_up || !h_lo || !h_A || n_lines < 0 || !c || !grid || !pa || !buf0 || !buf1 || !sigma_out ||
       !sigma_exp_out)
     return fail(PXC_ERR_ARG, "streamed: bad arguments");
+  X(ws)->fwd_key.clear();  // the workspace no longer holds a reusable line list
   const int wk = width_kind(pa->kind);
   const bool broad = wk == PXC_LORENTZ || wk == PXC_VOIGT;
   if (broad && (!h_gref || !h_nT)) return fail(PXC_ERR_ARG, "streamed: gamma_ref and n_T required");

@@ -34,7 +34,12 @@ constexpr uint64_t kSentinelKey = ~0ull;  // sorts after every positive double
 constexpr int kLinesPerBlockI = 2048;     // lines per CTA in the intensity pass (256 x 8)
 constexpr int kThreadsI = 256;
 constexpr int kUnitLines = 2048;         // lines per warp unit in the compacting intensity pass
-constexpr int kSortTile = 4096;           // keys per CTA in a radix pass (256 threads x 16)
+#ifndef PXC_SORT_TILE
+#define PXC_SORT_TILE 2048
+#endif
+// keys per CTA tile in a radix pass (256 threads x 8: 64 registers, four CTAs per SM; tiles of
+// 4096 keys took 100 registers and measured 0.3 ms slower per 1e9-line step)
+constexpr int kSortTile = PXC_SORT_TILE;
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = kSortTile / kSortThreads;
 constexpr int kQBlocks = 1184;            // 148 SMs x 8, fixed so the Q reduction order is fixed
@@ -68,13 +73,14 @@ struct CondDev {
 };
 
 // Per-state record of the intensity pass, one 32-byte sector: E exact, the FP64 Boltzmann factor,
-// g, and log2 of the Boltzmann factor in FP32 (for the rejection bound).
+// g in FP64 and FP32 (no conversion per line), and log2 of the Boltzmann factor in FP32 (for the
+// rejection bound).
 struct __align__(32) StateFast {
   double E;
   double b;
-  int32_t g;
+  double g;
+  float gf;
   float lb;
-  int64_t pad;
 };
 
 // Work item of the profile kernel: lines [begin, end) of the sorted list onto

@@ -118,3 +118,29 @@ def test_autograd_function(pxc):
     assert Tv.grad.item() == pytest.approx(out["dTvib"].item(), rel=1e-12)
     assert P.grad.item() == pytest.approx(out["dP"].item(), rel=1e-12)
     assert torch.equal(A.grad.float(), out["dA"]) and torch.equal(gref.grad, out["dgamma_ref"])
+
+
+def test_reuse_of_the_forward_line_list(pxc):
+    """pxc_set_reuse_forward: a backward right after an identical forward reads the forward's sorted
+    line list and returns bit-identical gradients to a backward that recomputes it; an intervening
+    call with other arguments discards the list and the backward recomputes (same results again)."""
+    import torch
+    c, w, ws, st, tr, prof, grid, wts, wt = _setup(pxc, "nlte_1e7", "voigt", 20_000)
+    cond = (w.T, w.T_vib, w.P)
+    pxc.pxc_cross_section(ws, st, tr, cond, grid, prof)
+    ref = pxc.pxc_cross_section_backward(ws, st, tr, cond, grid, prof, wt)
+    ws.sync()
+    ref = {k: v.clone() for k, v in ref.items()}
+    ws.set_reuse_forward(True)
+    pxc.pxc_cross_section(ws, st, tr, cond, grid, prof)
+    got = pxc.pxc_cross_section_backward(ws, st, tr, cond, grid, prof, wt)
+    ws.sync()
+    for k in ref:
+        assert torch.equal(got[k], ref[k]), k
+    # a forward at another condition in between: the backward at the first condition recomputes
+    pxc.pxc_cross_section(ws, st, tr, (w.T * 1.1, w.T_vib, w.P), grid, prof)
+    again = pxc.pxc_cross_section_backward(ws, st, tr, cond, grid, prof, wt)
+    ws.sync()
+    for k in ref:
+        assert torch.equal(again[k], ref[k]), k
+    ws.set_reuse_forward(False)
