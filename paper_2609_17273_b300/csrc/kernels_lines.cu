@@ -344,17 +344,27 @@ __device__ __forceinline__ QuantHdr quant_header(const unsigned long long* words
   return h;
 }
 
-__device__ __forceinline__ int quant_code(double e, const QuantHdr& h) {
-  if (!h.enabled || !isfinite(e)) return kCodeNone;
-  const double x = floor((e - h.Emin) * h.inv_res);
-  return x < 0.0 ? 0 : (x > (double)kCodeMax ? kCodeMax : (int)x);
+// q = floor((E - Emin) inv_res) within one code of the exact value, which the bounds' slack of one
+// code below and two above absorbs: E - Emin in FP64 (no cancellation), the scaling in FP32
+// (relative error ~1e-7 of at most 4094 codes), so two FP64-pipe operations per state.  Energy
+// spans beyond ~4e33 (FP32 would overflow) scale in FP64.
+__device__ __forceinline__ int quant_code(double e, const QuantHdr& h, float inv_res_f) {
+  const unsigned long long eb = (unsigned long long)__double_as_longlong(e);
+  if (!h.enabled || (eb & 0x7ff0000000000000ull) == 0x7ff0000000000000ull) return kCodeNone;  // inf, NaN
+  const float x = inv_res_f > 1e-30f ? floorf((float)(e - h.Emin) * inv_res_f)
+                                     : (float)floor((e - h.Emin) * h.inv_res);
+  return x < 0.f ? 0 : (x > (float)kCodeMax ? kCodeMax : (int)x);
 }
 
-// One thread per pair of states: the two 12-bit codes in three bytes.
+// One thread per 64-bit word: the 12-bit codes of five consecutive states.
 __global__ void __launch_bounds__(256) k_state_quant(const double* __restrict__ E, int64_t n,
                                                      const unsigned long long* __restrict__ words,
                                                      code_t* __restrict__ code, QuantHdr* __restrict__ hdr) {
-  const QuantHdr h = quant_header(words);
+  __shared__ QuantHdr hs;
+  if (threadIdx.x == 0) hs = quant_header(words);  // once per CTA (FP64 division and log2)
+  __syncthreads();
+  const QuantHdr h = hs;
+  const float inv_res_f = (float)h.inv_res;
   if (blockIdx.x == 0 && threadIdx.x == 0) *hdr = h;
   const int64_t nw = (n + 4) / 5;
   for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x) {
@@ -362,7 +372,7 @@ __global__ void __launch_bounds__(256) k_state_quant(const double* __restrict__ 
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
       const int64_t st = 5 * w + i;
-      const int q = st < n ? quant_code(E[st], h) : kCodeNone;
+      const int q = st < n ? quant_code(E[st], h, inv_res_f) : kCodeNone;
       word |= (code_t)q << (12 * i);
     }
     code[w] = word;
@@ -477,8 +487,8 @@ void launch_lines(const pxc_transitions* tr, const int32_t* g, int64_t ns, const
 // LTE (b_l - b_u = b_l (1 - e^{-c2 nu/T})) and m = 1 for two temperatures, evaluated in log2
 // units with a 1e-3 margin that covers every FP32 rounding in it.
 //
-// Before any 16-byte state record is read, a prefilter on the 12-bit state codes (1.5 bytes per
-// state, 75 MB for 5e7 states, mostly found in L2) rejects lines whose nu is
+// Before any 32-byte state record is read, a prefilter on the 12-bit state codes (1.6 bytes per
+// state, 80 MB for 5e7 states, about half of it found in L2) rejects lines whose nu is
 // certainly outside the kept window, and, for LTE with a threshold, lines whose intensity is
 // certainly below it: nu_lo = (d - 3) res, nu_hi = (d + 3) res with d = q_u - q_l, b_l <=
 // exp(-c2 E_lo(q_l) / T), g_u <= max g.  Only the surviving candidates gather their states.
@@ -599,7 +609,7 @@ __device__ __forceinline__ bool line_test(const LineIn& x, int A32, int64_t ns, 
 // (one warp per unit of kUnitLines consecutive lines) and writes each unit's candidates, in line
 // order, to the unit's range of three candidate arrays; it holds few registers, so the random
 // code gathers it waits on have the whole SM's worth of warps in flight.  The exact pass then
-// takes each unit's candidates 32 at a time on full warps: the 16-byte state records, exact nu and
+// takes each unit's candidates 32 at a time on full warps: the 32-byte state records, exact nu and
 // window, the FP32 bound with the exact log2 b, then the FP64 test |num| >= S_min nu^2 and
 // I = num / nu^2; kept lines go to the unit's staging range in line order, counted per unit.
 // When the codes are off (a list whose energies span far more than the kept window) the exact

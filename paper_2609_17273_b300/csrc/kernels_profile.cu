@@ -482,8 +482,9 @@ __device__ __forceinline__ int line_class(const LineC& c, int a) {
 //   K (u + 1) / (u^2 + e) = (K / |z|^2) (|z|^4 + |z|^2 / 2) / (|z|^4 - x^2 + y^2 + 1/4)
 //                         = (K / |z|^2) (1 + (3 x^2 - y^2) / (2 |z|^4) + O(|z|^-4)),
 // so the limit is within 1.5 / |z|^2 <= 3e-5 of it (relative).  Such a line is marked by d < 0 and
-// carries B1 = sigma^2 y^2 (its scaled denominator is x'^2 + B1); two of them cost eight FP32
-// instructions and one reciprocal per point, against twelve and one for two region-I lines.
+// carries B1 = sigma^2 y^2 (its scaled denominator is x'^2 + B1); the staging keeps it as the
+// float4 {a, b, B1, K}.  Two of them cost eight FP32 instructions and one reciprocal per point,
+// against twelve and one for two region-I lines.
 #ifndef PXC_LORENTZ_R2
 #define PXC_LORENTZ_R2 5e4f
 #endif
@@ -527,15 +528,6 @@ __device__ __forceinline__ void eval_fast(const LineC& c, const float* lk, float
     // reciprocal per point); no point of this warp is near the centre, so x = x(lane 0) + m step
     // keeps full relative accuracy
     const float KA = c.KA;  // K sigma^4, the rescaled numerator's constant term
-    if (f0.w < 0.f) {
-      // Lorentzian limit (see scale_for_pairs)
-#pragma unroll
-      for (int k = 0; k < PTS; ++k) {
-        const float x = fmaf(lk[k], f0.y, f0.x);
-        acc[k] = fmaf(K, frcp(fmaf(x, x, f0.z)), acc[k]);
-      }
-      return;
-    }
 #pragma unroll
     for (int k = 0; k < PTS; ++k) {
       const float x = fmaf(lk[k], f0.y, f0.x);
@@ -567,31 +559,6 @@ __device__ __forceinline__ void eval_fast2(const LineC& c, const LineC& e, const
   if (KIND == PXC_VOIGT) {
     const float4 a0 = *reinterpret_cast<const float4*>(&c.a), a1 = *reinterpret_cast<const float4*>(&c.K);
     const float4 b0 = *reinterpret_cast<const float4*>(&e.a), b1 = *reinterpret_cast<const float4*>(&e.K);
-    const bool lc = a0.w < 0.f, le = b0.w < 0.f;  // Lorentzian limits (the same for every lane)
-    if (lc && le) {
-      // K_c / d_c + K_e / d_e, d = x'^2 + sigma^2 y^2 (four FP32 operations and half a MUFU per evaluation)
-#pragma unroll
-      for (int k = 0; k < PTS; ++k) {
-        const float x = fmaf(lk[k], a0.y, a0.x), y = fmaf(lk[k], b0.y, b0.x);
-        const float du = fmaf(x, x, a0.z), dv = fmaf(y, y, b0.z);
-        acc[k] = fmaf(fmaf(b1.x, du, a1.x * dv), frcp(du * dv), acc[k]);
-      }
-      return;
-    }
-    if (lc || le) {
-      // one region-I line (r) and one in the Lorentzian limit (q)
-      const float4 r0 = lc ? b0 : a0, r1 = lc ? b1 : a1, q0 = lc ? a0 : b0;
-      const float Kq = lc ? a1.x : b1.x;
-#pragma unroll
-      for (int k = 0; k < PTS; ++k) {
-        const float x = fmaf(lk[k], r0.y, r0.x), y = fmaf(lk[k], q0.y, q0.x);
-        const float u = fmaf(x, x, r0.z);
-        const float du = fmaf(u, u, r0.w), dv = fmaf(y, y, q0.z);
-        const float nu = fmaf(u, r1.x, r1.y);
-        acc[k] = fmaf(fmaf(Kq, du, nu * dv), frcp(du * dv), acc[k]);
-      }
-      return;
-    }
 #pragma unroll
     for (int k = 0; k < PTS; ++k) {
       const float x = fmaf(lk[k], a0.y, a0.x), y = fmaf(lk[k], b0.y, b0.x);
@@ -604,6 +571,27 @@ __device__ __forceinline__ void eval_fast2(const LineC& c, const LineC& e, const
   } else {
     eval_fast<KIND, PTS>(c, lk, acc);
     eval_fast<KIND, PTS>(e, lk, acc);
+  }
+}
+
+// Lorentzian-limit Voigt lines from their 16-byte front records {a, b, sigma^2 y^2, K}.
+template <int PTS>
+__device__ __forceinline__ void eval_lor2(const LineC& c, const LineC& e, const float* lk, float* acc) {
+  const float4 a = *reinterpret_cast<const float4*>(&c.a), b = *reinterpret_cast<const float4*>(&e.a);
+#pragma unroll
+  for (int k = 0; k < PTS; ++k) {
+    const float x = fmaf(lk[k], a.y, a.x), y = fmaf(lk[k], b.y, b.x);
+    const float du = fmaf(x, x, a.z), dv = fmaf(y, y, b.z);
+    acc[k] = fmaf(fmaf(b.w, du, a.w * dv), frcp(du * dv), acc[k]);
+  }
+}
+template <int PTS>
+__device__ __forceinline__ void eval_lor1(const LineC& c, const float* lk, float* acc) {
+  const float4 a = *reinterpret_cast<const float4*>(&c.a);
+#pragma unroll
+  for (int k = 0; k < PTS; ++k) {
+    const float x = fmaf(lk[k], a.y, a.x);
+    acc[k] = fmaf(a.w, frcp(fmaf(x, x, a.z)), acc[k]);
   }
 }
 
@@ -793,11 +781,13 @@ __device__ __forceinline__ void eval_slow(const LineC& c, int wbase, int lane, c
   }
 }
 
-// Forward kernel.  The CTA's warps share kNB bulk-copy stage buffers of SL lines; each
-// warp turns every staged record into its own line constants and class (so no CTA barrier
-// is needed inside a work item), keeping two in-order lists in private shared memory: the
-// fast lines from the front, the others from the back.  The last warp to finish reading a
-// stage buffer re-arms it with the copy kNB stages ahead, so warps drift apart by up to
+// Forward kernel.  The CTA's warps share kNB bulk-copy stage buffers of SL lines; each warp turns
+// every staged record into its own line constants and class (so no CTA barrier is needed inside a
+// work item), keeping two in-order lists in private shared memory.  From the front: the fast
+// lines whose record is one float4 (Voigt: the Lorentzian-limit lines, evaluated in pairs with no
+// per-pair test; other kinds: every fast line).  From the back: the rest (Voigt region-I fast
+// lines, paired when adjacent, and the edge, mid and core classes).  The last warp to finish
+// reading a stage buffer re-arms it with the copy kNB stages ahead, so warps drift apart by up to
 // kNB - 1 stages instead of waiting for each other at every stage.
 // Stage buffers per CTA: three for multi-warp CTAs (warps drift by up to two stages); two for
 // one-warp CTAs, whose single warp never waits for another (the smaller shared-memory footprint
@@ -913,10 +903,16 @@ __global__ void __launch_bounds__(THREADS, MINB) k_profile(const ProfP p) {
           if (dmax * c.step > 1e9f || c.y > 1e9f) c.masks |= kWideRange;
           if (dmax * c.step < 1e4f && c.y < 15.f) c.masks |= kRegion2Everywhere;
         }
-        const unsigned bf = __ballot_sync(0xffffffffu, cls == 1);
-        const unsigned bo = __ballot_sync(0xffffffffu, cls >= 2);  // cls: the class before the range flag
-        if (cls == 1) my[nf + __popc(bf & lt)] = c;
-        if (cls >= 2) my[SL - 1 - (no + __popc(bo & lt))] = c;
+        // front: lines whose fast record is one float4 (Voigt: the Lorentzian limit {a, b, s^2 y^2, K};
+        // other kinds: every fast line); back: Voigt region-I fast lines and the other classes
+        const bool front = cls == 1 && (KIND != PXC_VOIGT || c.d < 0.f);
+        const unsigned bf = __ballot_sync(0xffffffffu, front);
+        const unsigned bo = __ballot_sync(0xffffffffu, cls >= 1 && !front);
+        if (front) {
+          if (KIND == PXC_VOIGT) *reinterpret_cast<float4*>(&my[nf + __popc(bf & lt)]) = make_float4(c.a, c.b, c.B1, c.K);
+          else my[nf + __popc(bf & lt)] = c;
+        }
+        if (cls >= 1 && !front) my[SL - 1 - (no + __popc(bo & lt))] = c;
         nf += __popc(bf);
         no += __popc(bo);
       }
@@ -937,12 +933,24 @@ __global__ void __launch_bounds__(THREADS, MINB) k_profile(const ProfP p) {
 #pragma unroll
       for (int k = 0; k < PTS; ++k) acc[k] = 0.f;
       int i = 0;
-      for (; i + 1 < nf; i += 2) eval_fast2<KIND, PTS>(my[i], my[i + 1], lk, acc);
-      if (i < nf) eval_fast<KIND, PTS>(my[i], lk, acc);
+      if (KIND == PXC_VOIGT) {
+        for (; i + 1 < nf; i += 2) eval_lor2<PTS>(my[i], my[i + 1], lk, acc);
+        if (i < nf) eval_lor1<PTS>(my[i], lk, acc);
+      } else {
+        for (; i + 1 < nf; i += 2) eval_fast2<KIND, PTS>(my[i], my[i + 1], lk, acc);
+        if (i < nf) eval_fast<KIND, PTS>(my[i], lk, acc);
+      }
       for (int q = SL - 1; q >= SL - no; --q) {
         const LineC& c = my[q];
         const int cls = c.masks & 7;
-        if (cls == 2) eval_fastmask<KIND, PTS>(c, wbase, lane, acc);
+        if (KIND == PXC_VOIGT && cls == 1) {
+          if (q - 1 >= SL - no && (my[q - 1].masks & 7) == 1) {
+            eval_fast2<KIND, PTS>(c, my[q - 1], lk, acc);
+            --q;
+          } else {
+            eval_fast<KIND, PTS>(c, lk, acc);
+          }
+        } else if (cls == 2) eval_fastmask<KIND, PTS>(c, wbase, lane, acc);
         else if (cls == 4) eval_mid<KIND, PTS>(c, wbase, lane, acc);
         else eval_slow<KIND, PTS>(c, wbase, lane, lk, acc);
       }
@@ -1184,11 +1192,11 @@ void launch_profile_wl(const ProfP& p, int64_t max_items, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ adjoint
-// One warp per batch of 32 consecutive sorted lines.  Lane q loads line q and builds its widths;
-// for each line of the batch in turn the lanes stride over its window (the line's values broadcast
-// by shuffles), recompute the profile and its width derivatives at each point and accumulate them
-// against w = dL/dsigma_s; a butterfly sum leaves the totals in every lane and lane q keeps line
-// q's.  With G = sum w f, Da = sum w df/dalpha, Dg = sum w df/dgamma (times the scaled intensity
+// Each warp takes batches of 32 sorted lines, strided across the warps.  Lane q loads line q and
+// builds its widths; for each line of the batch in turn the lanes stride over its window (the
+// line's values broadcast by shuffles), recompute the profile and its width derivatives at each
+// point and accumulate them against w = dL/dsigma_s; a butterfly sum leaves the totals in every
+// lane and lane q keeps line q's.  With G = sum w f, Da = sum w df/dalpha, Dg = sum w df/dgamma (times the scaled intensity
 // I_s) the chain rule gives
 //   dL/dA_l = I_s G / A_l,  dL/dgamma_ref_l = I_s (T_ref/T)^n P Dg,
 //   per-line shares of dL/dT (T_rot), dL/dT_vib and dL/dP (FP64, reduced in a fixed order),
@@ -1199,11 +1207,13 @@ template <int KIND>
 __global__ void __launch_bounds__(256) k_adjoint(const AdjP p) {
   const int lane = threadIdx.x & 31;
   const int64_t n = (int64_t)*p.n_dev;
-  const int64_t nbatch = (n + 31) >> 5;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const float dnu_f = (float)p.dnu;
-  for (int64_t bt = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; bt < nbatch; bt += warps) {
-    const int64_t j = bt * 32 + lane;
+  // warp gw takes lines gw, gw + W, gw + 2W, ... (W warps), 32 of them per batch: lines that crowd
+  // one wavenumber (consecutive in the sorted order) spread over many warps
+  for (int64_t b0 = gw; b0 < n; b0 += 32 * warps) {
+    const int64_t j = b0 + (int64_t)lane * warps;
     const bool valid = j < n;
     int4 p4 = make_int4(0, 0, 0, -1);
     float2 pr = make_float2(0.f, 0.f);
