@@ -43,12 +43,12 @@ EVAL_FP32_FMAS = 5
 EVAL_MUFU = 1
 L2_BYTES = 126 * 2 ** 20
 
-# DRAM traffic per launch from a committed ncu capture, valid only for the kernel source it was
-# taken on (sha256 prefix of the .cu file); scaled to one 1e8-line launch of voigt_1e9 from the
-# 2e7-line capture (profiles/k_profile_voigt_2e7_lines.md, profiles/k_lines_voigt_2e7_lines.md).
+# DRAM traffic per launch from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum),
+# valid only for the kernel source it was taken on (sha256 prefix of the .cu file); scaled by lines
+# to one 1e8-line launch of voigt_1e9 from the capture of its first 2e7 lines.
 NCU_TRAFFIC = {
-    ("profile", "a4ed75d62ec9c499"): 13.80e6 * 5,               # k_profile<voigt>, tile 0
-    ("intensity", "71d21a09c89640eb"): (793.9e6 + 383.2e6) * 5,  # k_lines_pre + k_lines_exact
+    ("profile", "d72efc4fdc838484"): 13.79e6 * 5,               # k_profile<voigt>, tile 0
+    ("intensity", "8c3f7be0522499e0"): (950.8e6 + 317.4e6) * 5,  # k_lines_pre + k_lines_exact
 }
 
 
