@@ -48,7 +48,7 @@ L2_BYTES = 126 * 2 ** 20
 # to one 1e8-line launch of voigt_1e9 from the capture of its first 2e7 lines.
 NCU_TRAFFIC = {
     ("profile", "d72efc4fdc838484"): 13.79e6 * 5,               # k_profile<voigt>, tile 0
-    ("intensity", "8c3f7be0522499e0"): (950.8e6 + 317.4e6) * 5,  # k_lines_pre + k_lines_exact
+    ("intensity", "d925ec9669974a9d"): (950.5e6 + 317.5e6) * 5,  # k_lines_pre + k_lines_exact
 }
 
 

@@ -322,7 +322,7 @@ pxc_status pxc_get_timing(pxc_workspace* ws, cudaStream_t stream, double* ms, in
  * and every one gives the same sigma up to FP32 summation order.  Wavelength grids always
  * use 128-point segments.  The workspace
  * keeps one tile per profile kind for single-condition calls (batched = 0,
- * default tile 0) and one for batched tables (batched = 1, default tile 3). */
+ * default tile 0) and one for batched tables (batched = 1, default tile 0). */
 #define PXC_NUM_TILES 4
 pxc_status pxc_set_tile(pxc_workspace* ws, int32_t kind, int32_t batched, int32_t tile);
 pxc_status pxc_get_tile(pxc_workspace* ws, int32_t kind, int32_t batched, int32_t* tile);

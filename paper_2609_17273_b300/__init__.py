@@ -88,7 +88,7 @@ ABI_FUNCTIONS = [
 # Profile-kernel tile configurations (segment width in grid points), as compiled into the library.
 NUM_TILES = 4
 TILE_SEGMENT_POINTS = (128, 256, 1024, 2048)
-BATCHED_DEFAULT_TILE = 3
+BATCHED_DEFAULT_TILE = 0
 
 
 def load(path: str | None = None):

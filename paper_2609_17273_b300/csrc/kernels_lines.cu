@@ -1121,8 +1121,10 @@ __global__ void __launch_bounds__(256) k_prepare(const uint64_t* __restrict__ sk
     int64_t a = 0, b = -1;
     exact_window(nu, gp, &a, &b);
     // position in grid steps: (nu - nu_min)/dnu, or (U/nu - lambda_min)/dlambda on a wavelength grid
-    const double coord = gp.wl_unit > 0.0 ? __ddiv_rn(gp.wl_unit, nu) : nu;
-    double c = __ddiv_rn(__dsub_rn(coord, gp.nu_min), gp.dnu);
+    // (on a wavenumber grid by the reciprocal: the position only places the profile's centre, and
+    // a last-bit difference moves it by ~1e-16 of its value; the window above is exact)
+    double c = gp.wl_unit > 0.0 ? __ddiv_rn(__dsub_rn(__ddiv_rn(gp.wl_unit, nu), gp.nu_min), gp.dnu)
+                                : __dsub_rn(nu, gp.nu_min) * gp.inv_dnu;
     double fc = floor(c);
     float f = (float)__dsub_rn(c, fc);
     pos[j] = make_int4((int)fc, __float_as_int(f), (int)a, (int)b);

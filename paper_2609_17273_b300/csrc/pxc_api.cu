@@ -457,8 +457,8 @@ pxc_status pxc_workspace_create(const pxc_capacity* cap, void* scratch, size_t b
   }
   for (int k = 0; k < kNumKinds; ++k) {
     for (int t = 0; t < kNumTiles; ++t) x->occ[k][t] = profile_occupancy(k, t);
-    // defaults: narrow segments balance dense single-condition spectra best; batched
-    // tables (most lines zero in most conditions) pay less staging with wide segments
+    // defaults: narrow segments balance dense spectra best, for single-condition calls and for
+    // batched tables (which profile each temperature's non-zero lines only)
     x->tile[k][0] = 0;
     x->tile[k][1] = kBatchedDefaultTile;
   }

@@ -48,7 +48,7 @@ constexpr int kThreadsQ = 256;
 // Profile kernel tiles: segment widths are a runtime choice among the compiled configurations
 // (see kernels_profile.cu); the workspace is sized for the narrowest and the widest.
 constexpr int kNumTiles = 4;
-constexpr int kBatchedDefaultTile = 3;  // 2048-point segments
+constexpr int kBatchedDefaultTile = 0;  // 128-point segments (each temperature's non-zero lines only)
 constexpr int kNumKinds = 11;
 // Profile kinds (pxc_profile): sampled 0..3, binned 4..7, pseudo-Voigt 8..10.
 __host__ __device__ constexpr bool is_binned(int kind) { return kind >= 4 && kind <= 7; }
